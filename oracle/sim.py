@@ -1,0 +1,139 @@
+"""One EM-PIC cycle in the order of Sec. 3, FP64.  Test infrastructure.
+
+State at the start of step n: E^n (edges), B^{n-1/2} (faces), particle positions r^n
+(triangle + barycentric lambda), momenta u^{n-1/2}, node charges Q^n.
+  1. B^{n+1/2} = B^{n-1/2} - dt D_curl E^n                        (Eq. full_d_dfl)
+  2. gather E^n and (B^{n+1/2} + B^{n-1/2})/2 at r^n, Boris push, walk, scatter
+     J^{n+1/2} (Eq. current) and Q^{n+1} (Eq. charge)              (Secs. 3.2-3.4)
+  3. E^{n+1} = E^n + dt M (D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}) (Eq. full_d_dal)
+The auxiliary dual flux D^{n+1} = D^n + dt (D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}) is
+carried for the discrete Gauss law check: D_div D^n - Q^n is constant in n (Sec. 3.5.2).
+"""
+import math
+
+import numpy as np
+
+from .operators import Mesh, hodge_eps, hodge_mu_inv, spai, dt_stable, field_energy
+from . import particles as P
+
+
+class OracleSim:
+    def __init__(self, nodes, tris, bedges, btags, eps0=1.0, mu0=1.0, c=None,
+                 level=2, drop_tol=1e-4, M=None):
+        self.mesh = Mesh(nodes, tris, bedges, btags)
+        self.eps0, self.mu0 = eps0, mu0
+        self.c = c if c is not None else 1.0 / math.sqrt(eps0 * mu0)
+        self.star_eps = hodge_eps(self.mesh, eps0)
+        self.mu_inv = hodge_mu_inv(self.mesh, mu0)
+        self.M = spai(self.mesh, self.star_eps, level, drop_tol) if M is None else M
+        self.dt_max, self.lam_max = dt_stable(self.mesh, self.M, self.mu_inv)
+        self.pm = P.PushMesh(self.mesh)
+        m = self.mesh
+        self.E = np.zeros(m.N1)
+        self.B = np.zeros(m.N2)            # B^{n-1/2}
+        self.D = np.zeros(m.N1)
+        self.Q = np.zeros(m.N0)
+        self.Q_prev = np.zeros(m.N0)
+        self.J = np.zeros(m.N1)
+        self.Qabs = np.zeros(m.N0)
+        self.tri = np.zeros(0, np.int32)
+        self.lam = np.zeros((0, 3))
+        self.u = np.zeros((0, 3))
+        self.qm = 0.0
+        self.q_src = 0.0
+        self.q = self.mass = self.weight = 0.0
+        self.dt = None
+        self.bz = 0.0
+        self.counters = np.zeros(3, np.int64)
+        self.n = 0
+
+    def create(self, dt, bz=0.0):
+        if dt > self.dt_max:
+            raise ValueError("dt above the stable limit")
+        self.dt, self.bz = float(dt), float(bz)
+
+    def set_fields(self, E, B_half_prev):
+        E = np.array(E, float)
+        E[self.mesh.edge_tag == 1] = 0.0
+        self.E = E
+        self.B = np.array(B_half_prev, float)
+        self.D = self.star_eps @ self.E
+
+    def inject(self, z, rho, ur, up, uz, q, mass, weight):
+        """Locate the particles, append them, and add their charge to Q^n."""
+        if self.q_src != 0.0 and (q / mass != self.qm or weight * q / (2 * math.pi) != self.q_src):
+            raise ValueError("one species per simulation")
+        self.q, self.mass, self.weight = q, mass, weight
+        self.qm = q / mass
+        # ring normalisation: the 2D equations are the 3D ones divided by 2 pi
+        self.q_src = weight * q / (2.0 * math.pi)
+        tri, lam = P.locate(self.mesh, z, rho)
+        if np.any(tri < 0):
+            raise ValueError("particle outside the mesh")
+        u = np.stack([ur, up, uz], 1).astype(float)
+        P.deposit_charge(self.pm, tri, np.ascontiguousarray(lam), self.q_src, self.Q)
+        self.tri = np.ascontiguousarray(np.concatenate([self.tri, tri]).astype(np.int32))
+        self.lam = np.ascontiguousarray(np.concatenate([self.lam, lam]))
+        self.u = np.ascontiguousarray(np.concatenate([self.u, u]))
+
+    def field_b_half(self):
+        """Eq. full_d_dfl."""
+        return self.B - self.dt * (self.mesh.Dcurl @ self.E)
+
+    def push_particles(self, B_half):
+        m = self.mesh
+        Bavg = 0.5 * (B_half + self.B)
+        self.J = np.zeros(m.N1)
+        Qn = np.zeros(m.N0)
+        self.Qabs = np.zeros(m.N0)
+        cnt = P.push(self.pm, self.E, Bavg, self.bz, self.dt, self.qm, self.c, self.q_src,
+                     self.tri, self.lam, self.u, self.J, Qn, self.Qabs)
+        self.counters += cnt
+        return Qn
+
+    def field_e(self, B_half):
+        """Eq. full_d_dal with [star_eps]^-1 replaced by the SPAI matrix M."""
+        m = self.mesh
+        f = m.free
+        r = m.Dcurl.T @ (self.mu_inv * B_half) - self.J
+        self.D[f] += self.dt * r[f]
+        self.E[f] += self.dt * (self.M @ r[f])
+
+    def step(self, n=1):
+        for _ in range(n):
+            B_half = self.field_b_half()
+            Qn = self.push_particles(B_half)
+            self.field_e(B_half)
+            self.B = B_half
+            self.Q_prev, self.Q = self.Q, Qn
+            self.n += 1
+
+    # ---- diagnostics (Sec. 3.5, Sec. 5.1.1) ----
+    def dce_residual(self):
+        """(Q^{n+1} - Q^n + Q_absorbed)/dt + D_div J^{n+1/2}, per node (Eq. DCE)."""
+        return (self.Q - self.Q_prev + self.Qabs) / self.dt + self.mesh.Ddiv @ self.J
+
+    def dgl_residual(self):
+        """D_div D^n - Q^n at nodes not on a conducting wall (Eq. DGL_RSD_REL)."""
+        m = self.mesh
+        f = m.free
+        res = m.Ddiv[:, f] @ self.D[f] - self.Q
+        res[m.node_on_pec] = 0.0
+        return res
+
+    def field_energy(self):
+        return field_energy(self.mesh, self.star_eps, self.mu_inv, self.E, self.B)
+
+    def kinetic_energy(self):
+        """Total kinetic energy of the macro-particles (3D), (gamma - 1) m c^2 w."""
+        live = self.tri >= 0
+        u2 = np.sum(self.u[live] ** 2, 1)
+        gam = np.sqrt(1.0 + u2 / self.c ** 2)
+        return float(np.sum((gam - 1.0)) * self.mass * self.weight * self.c ** 2)
+
+    def positions(self):
+        """Physical (z, rho) of live particles from (triangle, lambda)."""
+        live = self.tri >= 0
+        p = self.mesh.nodes[self.mesh.tris[self.tri[live]]]
+        zr = np.einsum("nk,nkd->nd", self.lam[live], p)
+        return zr[:, 0], zr[:, 1]

@@ -1,0 +1,79 @@
+"""Pins of the oracle's field solver: cavity resonances against the Bessel-zero closed
+form (Sec. 4.1, Table 1) and the stability limit of the leapfrog scheme.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import least_squares
+
+import workloads as W
+from oracle import OracleSim
+
+
+@pytest.fixture(scope="module")
+def cavity():
+    """The 0.5 x 1 normalised cavity (c = 1) with about 2000 triangles."""
+    return OracleSim(*W.cavity_mesh())
+
+
+def _two_tone_fit(t, a, w0, w1):
+    def res(p):
+        return (p[0] * np.cos(p[2] * t) + p[1] * np.sin(p[2] * t)
+                + p[3] * np.cos(p[5] * t) + p[4] * np.sin(p[5] * t) - a)
+    r = least_squares(res, [a[0], 0.0, w0, 0.0, 0.0, w1], x_scale="jac")
+    return r.x
+
+
+def test_cavity_tm010_tm011_frequencies(cavity):
+    """E^0 = TM010 + TM011 line integrals, B^{-1/2} = 0, 1000 steps at half the stable
+    step; the projections on the two mode patterns oscillate at the closed-form
+    frequencies omega = c sqrt((x_0n/a)^2 + (p pi/L)^2) within 0.5%."""
+    s = cavity
+    m = s.mesh
+    dt = 0.5 * s.dt_max
+    s.create(dt)
+    P0 = W.tm0np_edge_dofs(m.nodes, m.edge_nodes, 0.5, 1.0, 1, 0)
+    P1 = W.tm0np_edge_dofs(m.nodes, m.edge_nodes, 0.5, 1.0, 1, 1)
+    s.set_fields(P0 + P1, np.zeros(m.N2))
+    a0, a1 = [], []
+    for _ in range(1000):
+        a0.append(s.E @ P0)
+        a1.append(s.E @ P1)
+        s.step()
+    t = np.arange(1000) * dt
+    w010 = W.tm0np_omega(0.5, 1.0, 1, 0)
+    w011 = W.tm0np_omega(0.5, 1.0, 1, 1)
+    p0 = _two_tone_fit(t, np.array(a0), w010, w011)
+    p1 = _two_tone_fit(t, np.array(a1), w011, w010)
+    # the dominant tone of each projection
+    f0 = p0[2] if np.hypot(p0[0], p0[1]) > np.hypot(p0[3], p0[4]) else p0[5]
+    f1 = p1[2] if np.hypot(p1[0], p1[1]) > np.hypot(p1[3], p1[4]) else p1[5]
+    assert abs(f0 - w010) / w010 < 5e-3
+    assert abs(f1 - w011) / w011 < 5e-3
+
+
+def test_stability_limit(cavity):
+    """At half the estimated limit the field energy stays bounded; 20% above it the
+    leapfrog diverges."""
+    m = cavity.mesh
+    E0 = W.random_edge_values(m.N1, 1.0, 3)
+
+    def run(f, n):
+        s = OracleSim.__new__(OracleSim)
+        s.__dict__.update(cavity.__dict__)
+        s.dt = f * cavity.dt_max
+        s.set_fields(E0, np.zeros(m.N2))
+        s.J = np.zeros(m.N1)
+        e0 = s.field_energy()
+        emax = e0
+        for _ in range(n):
+            Bh = s.field_b_half()
+            s.field_e(Bh)
+            s.B = Bh
+            emax = max(emax, s.field_energy())
+            if emax > 1e8 * e0:
+                break
+        return emax / e0
+
+    assert run(0.5, 1000) < 2.0
+    assert run(1.2, 400) > 1e6
