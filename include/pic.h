@@ -1,0 +1,221 @@
+/*
+ * pic.h -- C ABI of the GB300 library for the axisymmetric charge-conservative
+ * electromagnetic particle-in-cell method on unstructured triangle meshes of the
+ * meridian (z, rho) plane (Na, Omelchenko, Moon, Borges, Teixeira, 2017).
+ *
+ * One simulation advances, per call of pic_step, the paper's cycle (Sec. 3):
+ *   B^{n+1/2} = B^{n-1/2} - dt D_curl E^n                                (Eq. full_d_dfl)
+ *   gather E^n and (B^{n+1/2}+B^{n-1/2})/2 at each particle by Whitney forms (Sec. 3.2),
+ *   relativistic Boris push (Eqs. DNE, DLE), triangle walk, charge-conserving scatter of
+ *   edge currents J^{n+1/2} (Eq. current) and node charges Q^{n+1} (Eq. charge),
+ *   E^{n+1} = E^n + dt M (D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2})      (Eq. full_d_dal)
+ * with M the sparse approximate inverse (SPAI) of the rho-weighted Hodge matrix star_eps.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a pic_status and never aborts the process.  On an error nothing
+ *    is written to the caller's output arrays and pic_last_error() returns a message
+ *    (thread-local, valid until the next failing call on the same thread).
+ *  - Handles are owned by the library and released by the matching *_destroy call.
+ *  - Input arrays are caller-owned host arrays; the library copies what it keeps.
+ *  - Output arrays are caller-owned host arrays of the stated size, unless stated.
+ *  - Units are the caller's, consistent with eps0, mu0 and c in pic_units.
+ *  - Mesh coordinates: nodes are (z, rho) pairs with rho >= 0.  Triangles are node
+ *    triples, any orientation (stored counter-clockwise in (z, rho)).  Edges are
+ *    oriented from the lower to the higher node index (App. D) and numbered in
+ *    lexicographic order of (lower, higher) node index; faces keep the input order.
+ *  - Field degrees of freedom: E_e is the line integral of E along edge e (Whitney
+ *    1-form), B_f the flux of B_phi through face f (Whitney 2-form, B_phi = B_f / A_f).
+ *  - Device memory comes from the allocator installed by pic_set_allocator, or from
+ *    cudaMalloc when none is installed.  All device work of a call is ordered on the
+ *    stream passed to it (NULL: the legacy default stream).
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_mesh pic_mesh; /* opaque: mesh, incidence, Hodge and SPAI operators */
+typedef struct pic_sim pic_sim;   /* opaque: device-resident fields and particles      */
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,      /* bad argument (null pointer, size, value out of range)       */
+    PIC_ERR_MESH = 2,     /* inconsistent mesh (degenerate triangle, bad boundary list)  */
+    PIC_ERR_CUDA = 3,     /* a CUDA runtime call failed                                  */
+    PIC_ERR_UNSTABLE = 4, /* dt above the stable leapfrog limit                          */
+    PIC_ERR_TIMEOUT = 5,  /* a bounded device wait gave up                               */
+    PIC_ERR_OOM = 6,      /* device or host allocation failed / capacity exceeded        */
+    PIC_ERR_STATE = 7     /* call out of order (e.g. pic_sim_create before SPAI)         */
+} pic_status;
+
+/* boundary tags of mesh boundary edges */
+enum {
+    PIC_BC_PEC = 1,   /* conductor: tangential E = 0 (edge DOF removed), particles absorbed */
+    PIC_BC_AXIS = 2,  /* rho = 0: natural (PMC) field condition, particles stay (Sec. 5.1)  */
+    PIC_BC_ABSORB = 3 /* open port: natural field condition, particles absorbed             */
+};
+
+/* arithmetic of the particle loop and fields */
+enum {
+    PIC_FP64 = 0, /* FP64 fields and particles, FP64 atomics for J and Q                   */
+    PIC_FP32 = 1  /* FP32 fields and momenta; positions as fixed-point barycentric
+                     coordinates (2^-22); J and Q as int64 fixed point (2^-44, 2^-22),
+                     so the scatter sums are exact and independent of order             */
+};
+
+typedef struct {
+    double eps0;       /* vacuum permittivity                                       */
+    double mu0;        /* vacuum permeability                                       */
+    double c;          /* speed of light (used in gamma = sqrt(1 + |u|^2/c^2))      */
+    int32_t precision; /* PIC_FP64 or PIC_FP32                                      */
+    int32_t walk_cap;  /* edge crossings per particle per step before the particle
+                          is removed and counted as a walk overflow; 0 means 16     */
+} pic_units;
+
+typedef struct {
+    int64_t n_particles;     /* live particles                                          */
+    int64_t n_absorbed;      /* particles removed at walls since creation                */
+    int64_t walk_overflows;  /* particles removed by the walk cap since creation         */
+    int64_t n_crossings;     /* edge crossings since creation                            */
+    int64_t n_steps;         /* steps taken                                              */
+    double dce_max;          /* max over nodes of |(Q^{n+1}-Q^n+Qabs)/dt + D_div J| of the
+                                last step, in units of q_src/dt (Eq. DCE)                 */
+    int64_t dce_nonzero;     /* FP32: nodes where the fixed-point DCE is not exactly 0  */
+    double nr_dce_max;       /* max |NR_DCE| of Sec. 5.1.1 over nodes with net current   */
+    double dgl_drift;        /* max over non-PEC nodes of |res^n - res^ref|, res^n =
+                                D_div D^n - Q^n (Eq. DGL_RSD_REL), relative to max|Q|;
+                                res^ref is taken at the first step after the host last
+                                changed fields or particles                               */
+    double field_energy;     /* 1/2 E.star_eps.E + 1/2 B.star_mu^-1.B (per radian)        */
+    double kinetic_energy;   /* sum (gamma-1) m c^2 w over live particles (3D)             */
+    double q_absorbed;       /* charge removed at walls since creation (3D, q*w units)   */
+} pic_diag;
+
+/* Allocator hook for device memory (e.g. a framework's caching allocator).  alloc must
+ * return device memory of at least `bytes` bytes aligned to 256 bytes, or NULL; free
+ * releases it.  Install before creating simulations; pass NULLs to restore cudaMalloc. */
+typedef void *(*pic_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*pic_free_fn)(void *ptr, void *ctx);
+pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_, void *ctx);
+
+/* Mesh of the meridian plane (Sec. 3.1, App. D).  nodes_zr: n_nodes x 2 doubles (z, rho);
+ * tris: n_tris x 3 node indices; bedge_nodes: n_bedges x 2 node indices, one row per
+ * boundary edge of the mesh (every edge with one triangle must be listed exactly once);
+ * bedge_tag: PIC_BC_* per boundary edge.  Builds the incidence matrices D_curl (N2 x N1)
+ * and D_div (N0 x N1), per-triangle geometry, the rho-weighted Hodge matrix star_eps
+ * (Eq. dis_hodge_eps, App. B; exact integration) and the diagonal star_mu^-1
+ * (Eq. dis_hodge_mu: rho_bar_f / (mu0 A_f)).  Host-only; no device memory yet.
+ * Errors: PIC_ERR_ARG (null / non-positive sizes / rho < 0 / bad index), PIC_ERR_MESH. */
+pic_status pic_mesh_create(const double *nodes_zr, int64_t n_nodes, const int32_t *tris,
+                           int64_t n_tris, const int32_t *bedge_nodes,
+                           const int32_t *bedge_tag, int64_t n_bedges, const pic_units *u,
+                           pic_mesh **out);
+
+/* Sizes: nodes N0, edges N1, faces N2, free (non-PEC) edges, nonzeros of M (0 before
+ * pic_spai_build).  Any pointer may be NULL. */
+pic_status pic_mesh_info(const pic_mesh *m, int64_t *n_nodes, int64_t *n_edges,
+                         int64_t *n_tris, int64_t *n_free_edges, int64_t *spai_nnz);
+
+/* Edge list in library numbering: n_edges x 2 node indices (tail, head). */
+pic_status pic_mesh_edges(const pic_mesh *m, int32_t *edge_nodes);
+
+/* SPAI of star_eps (Sec. 3.1: the explicit, local E update).  Column j of M minimises
+ * ||star_eps m - e_j||_2 over vectors supported on the free edges within
+ * `pattern_level` triangle-hops of edge j (a dense least-squares problem over the rows
+ * those columns touch); entries below drop_tol * max_i |m_i| are dropped and
+ * M <- (M + M^T)/2.  Then the stable step dt_max = 2 / sqrt(lambda_max(M K)),
+ * K = D_curl^T star_mu^-1 D_curl, by 500 power iterations, is written to *dt_stable_out
+ * (may be NULL).  pattern_level in [0, 8], drop_tol in [0, 1).  Host-only. */
+pic_status pic_spai_build(pic_mesh *m, int32_t pattern_level, double drop_tol,
+                          double *dt_stable_out);
+
+/* Optional: export the free-edge numbering and M in CSR (free-edge indices).
+ * free_edges: n_free entries (may be NULL); indptr: n_free+1; indices, values: nnz. */
+pic_status pic_spai_get(const pic_mesh *m, int32_t *free_edges, int64_t *indptr,
+                        int32_t *indices, double *values);
+
+/* Simulation on the current CUDA device: uploads the mesh operators and allocates
+ * fields and room for `max_particles` particles.  dt must not exceed the stable step
+ * from pic_spai_build (PIC_ERR_UNSTABLE otherwise); bz_guide is a uniform static axial
+ * magnetic field added at the gather (Sec. 3.2, beam focusing system).  The mesh must
+ * outlive the simulation.  Fields start at zero.  Errors: ARG, STATE (no SPAI), UNSTABLE,
+ * OOM, CUDA. */
+pic_status pic_sim_create(pic_mesh *m, double dt, double bz_guide, int64_t max_particles,
+                          pic_sim **out);
+
+/* Steps between particle re-sorts by triangle (default 4; 0 disables re-sorting). */
+pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
+
+/* Set E^n (N1 doubles; PEC entries are forced to 0) and B^{n-1/2} (N2 doubles); either
+ * may be NULL to leave it.  Resets the DGL auxiliary flux D = star_eps E. */
+pic_status pic_fields_set(pic_sim *s, const double *E_edges, const double *B_faces_half,
+                          void *cuda_stream);
+
+/* Inject n particles of one species: physical positions (z, rho) and momenta u = gamma v
+ * in the local (rho, phi, z) frame; charge q and mass m of the physical particle, and the
+ * macro-particle weight w.  The ring's source charge is q_src = w q / (2 pi), since the
+ * meridian-plane equations are the 3D ones divided by 2 pi.  Each particle is located on
+ * the host (the triangle with the largest smallest barycentric coordinate; ties to the
+ * lower triangle index), uploaded, and its charge is added to Q^n (Eq. charge).  Only one
+ * species per simulation: later calls must repeat q/m and w q.  Errors: ARG (point
+ * outside the mesh, species mismatch), OOM (capacity). */
+pic_status pic_particles_inject(pic_sim *s, int64_t n, const double *z, const double *rho,
+                                const double *u_rho, const double *u_phi, const double *u_z,
+                                double q, double m, double weight, void *cuda_stream);
+
+/* Advance n_steps full cycles on the stream (asynchronous: returns once enqueued). */
+pic_status pic_step(pic_sim *s, int64_t n_steps, void *cuda_stream);
+
+/* Synchronous diagnostics (Sec. 3.5, Sec. 5.1.1) and optional field read-back:
+ * E_out (N1), B_out (N2, B^{n-1/2}), J_out (N1, J^{n-1/2} of the last step in physical
+ * units), each may be NULL. */
+pic_status pic_diagnostics(pic_sim *s, pic_diag *out, double *E_out, double *B_out,
+                           double *J_out, void *cuda_stream);
+
+/* Node charges in physical units (N0 each, may be NULL): Q^n, Q^{n-1} and the charge
+ * absorbed at walls during the last step. */
+pic_status pic_charges_get(pic_sim *s, double *Q, double *Q_prev, double *Q_absorbed,
+                           void *cuda_stream);
+
+/* Number of particle slots in use (live and removed-but-not-yet-compacted). */
+pic_status pic_particles_count(pic_sim *s, int64_t *n_slots, void *cuda_stream);
+
+/* Particle state, synchronous: for each of the n_slots slots, pid (the 0-based global
+ * injection index), tri (-1 for removed particles), lambda (3 doubles) and u (3 doubles).
+ * n_cap is the capacity of the output arrays; PIC_ERR_ARG if n_slots > n_cap. */
+pic_status pic_particles_get(pic_sim *s, int64_t n_cap, int64_t *pid, int32_t *tri,
+                             double *lam, double *u, void *cuda_stream);
+
+/* Raw device state, for host round trips in the storage format: FP32 slots take 24 bytes
+ * (int32 tri, int32 lambda_0, int32 lambda_1 at 2^-22, float u_rho, u_phi, u_z), FP64
+ * slots 44 bytes (int32 tri, double lambda_0, lambda_1, u_rho, u_phi, u_z), stored as
+ * structure-of-arrays over n_slots: all tri values, then all lambda_0, and so on.
+ * pic_particles_raw_get copies the first n_slots slots device -> host (n_slots at most
+ * the count from pic_particles_count); pic_particles_raw_set copies n_slots slots host ->
+ * device and makes n_slots the slot count (at most the capacity; particle ids are kept).
+ * Both are asynchronous on the stream; host buffers should be page-locked. */
+pic_status pic_particles_raw_bytes(pic_sim *s, int64_t *bytes_per_particle);
+pic_status pic_particles_raw_get(pic_sim *s, void *host_dst, int64_t n_slots,
+                                 void *cuda_stream);
+pic_status pic_particles_raw_set(pic_sim *s, const void *host_src, int64_t n_slots,
+                                 void *cuda_stream);
+
+/* Device time of the particle kernel over the steps enqueued since the last call
+ * (CUDA events around each launch on the step's stream); synchronous.  Writes the
+ * total milliseconds and the number of launches. */
+pic_status pic_kernel_timing(pic_sim *s, int32_t enable, double *push_ms, int64_t *launches,
+                             void *cuda_stream);
+
+void pic_sim_destroy(pic_sim *s);
+void pic_mesh_destroy(pic_mesh *m);
+const char *pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -1,0 +1,106 @@
+// Field update of the mixed E-B leapfrog (Eqs. full_d_dfl, full_d_dal) and the per-step
+// triangle field records read by the particle kernel.
+#include "pic_internal.h"
+
+namespace pic {
+
+// K3, one thread per face: B^{n+1/2} = B^{n-1/2} - dt (D_curl E^n)_f, and the record's
+// field coefficients: E(lambda) = sum_k E_k (lambda_a grad lambda_b - lambda_b grad
+// lambda_a) = sum_m lambda_m c_m, and B_phi = (B^{n+1/2} + B^{n-1/2}) / (2A) (W2 = 1/A).
+template <class P>
+__global__ void __launch_bounds__(256) k_field_b(FieldArgs<P> a) {
+    using R = typename P::R;
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= a.N2) return;
+    TriRec<R> &rc = a.rec[f];
+    const int32_t flags = rc.flags;
+    R g[3][2] = {{rc.g[0], rc.g[1]}, {rc.g[2], rc.g[3]}, {-rc.g[0] - rc.g[2], -rc.g[1] - rc.g[3]}};
+    R c[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    R curl = 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        R Ek = a.E[rc.edge[k]];
+        int i = (k + 1) % 3, j = (k + 2) % 3;
+        bool fwd = (flags >> k) & 1;   // edge runs (k+1) -> (k+2): D_curl entry +1
+        int ta = fwd ? i : j, hb = fwd ? j : i;
+        c[ta][0] += Ek * g[hb][0];
+        c[ta][1] += Ek * g[hb][1];
+        c[hb][0] -= Ek * g[ta][0];
+        c[hb][1] -= Ek * g[ta][1];
+        curl += fwd ? Ek : -Ek;
+    }
+    R Bold = a.B[f];
+    R Bnew = Bold - a.dt * curl;
+    a.B[f] = Bnew;
+    rc.bphi = R(0.5) * (Bnew + Bold) * rc.inv_area;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        rc.c[2 * k] = c[k][0];
+        rc.c[2 * k + 1] = c[k][1];
+    }
+}
+
+// K4a, one thread per free edge: r = D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}; the DGL
+// auxiliary flux D += dt r.
+template <class P>
+__global__ void __launch_bounds__(256) k_field_r(FieldArgs<P> a) {
+    using R = typename P::R;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nf) return;
+    int32_t e = a.free_edges[i];
+    double r = 0;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        int32_t fs = a.edge_face[2 * e + q];
+        if (fs == 0) continue;
+        int32_t f = (fs > 0 ? fs : -fs) - 1;
+        double hf = (double)a.mu_inv[f] * (double)a.B[f];
+        r += fs > 0 ? hf : -hf;
+    }
+    double Jp;
+    if constexpr (P::fixed) Jp = (double)(long long)a.J[e] * a.j_scale;
+    else Jp = a.J[e] * a.j_scale;
+    r -= Jp;
+    a.D[e] += (double)a.dt * r;
+    a.r[i] = (R)r;
+}
+
+// K4b, sliced ELL SpMV over free edges: E_e += dt (M r)_i.  A warp owns a slice of 32 rows
+// stored column-major, so each step of the row loop reads 32 consecutive values.
+template <class P>
+__global__ void __launch_bounds__(256) k_field_spmv(FieldArgs<P> a) {
+    using R = typename P::R;
+    int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t slice = row >> 5;
+    int lane = (int)(row & 31);
+    int64_t n_slices = (a.nf + 31) >> 5;
+    if (slice >= n_slices) return;
+    int64_t off = a.ell_off[slice];
+    int width = (int)((a.ell_off[slice + 1] - off) >> 5);
+    R acc = 0;
+    for (int k = 0; k < width; k++) {
+        int64_t idx = off + ((int64_t)k << 5) + lane;
+        int32_t col = a.ell_col[idx];
+        acc += a.ell_val[idx] * a.r[col];
+    }
+    if (row < a.nf) a.E[a.free_edges[row]] += a.dt * acc;
+}
+
+template <class P>
+void launch_field_b(const FieldArgs<P> &a, cudaStream_t s) {
+    k_field_b<P><<<(unsigned)((a.N2 + 255) / 256), 256, 0, s>>>(a);
+}
+
+template <class P>
+void launch_field_e(const FieldArgs<P> &a, cudaStream_t s) {
+    k_field_r<P><<<(unsigned)((a.nf + 255) / 256), 256, 0, s>>>(a);
+    int64_t rows = ((a.nf + 31) / 32) * 32;
+    k_field_spmv<P><<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(a);
+}
+
+template void launch_field_b<PF32>(const FieldArgs<PF32> &, cudaStream_t);
+template void launch_field_b<PF64>(const FieldArgs<PF64> &, cudaStream_t);
+template void launch_field_e<PF32>(const FieldArgs<PF32> &, cudaStream_t);
+template void launch_field_e<PF64>(const FieldArgs<PF64> &, cudaStream_t);
+
+}  // namespace pic

@@ -1,0 +1,240 @@
+// Internal declarations of the GB300 PIC library: host mesh, device record layouts,
+// precision policies and kernel launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+// ---------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+#define PIC_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t err__ = (expr);                                                     \
+        if (err__ != cudaSuccess) {                                                     \
+            ::pic::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(err__), \
+                             __FILE__, __LINE__);                                       \
+            return PIC_ERR_CUDA;                                                        \
+        }                                                                               \
+    } while (0)
+
+// ---------------------------------------------------------------------------------
+// fixed point of the FP32 build
+// ---------------------------------------------------------------------------------
+// Barycentric coordinates are stored as integers in units of 2^-22 that sum to exactly
+// 2^22.  The current of a segment, lambda_a^s lambda_b^e - lambda_b^s lambda_a^e, is then
+// an exact integer in units of 2^-44 and node charges are integers in units of 2^-22:
+// every scatter sum is exact and independent of summation order, and the discrete
+// continuity equation holds identically in integers.
+constexpr int LAM_BITS = 22;
+constexpr int32_t LAM_ONE = 1 << LAM_BITS;
+constexpr double LAM_INV = 1.0 / (double)LAM_ONE;
+constexpr double J_INV = LAM_INV * LAM_INV;  // 2^-44
+
+// ---------------------------------------------------------------------------------
+// host mesh and operators
+// ---------------------------------------------------------------------------------
+struct HostMesh {
+    pic_units units{};
+    int64_t N0 = 0, N1 = 0, N2 = 0;
+    std::vector<double> zr;            // N0 x 2 (z, rho)
+    std::vector<int32_t> tri;          // N2 x 3, counter-clockwise in (z, rho)
+    std::vector<int32_t> tri_edge;     // N2 x 3, local edge k opposite local node k
+    std::vector<int32_t> tri_nbr;      // N2 x 3, neighbour across local edge k or -1
+    std::vector<int32_t> edge_nodes;   // N1 x 2 (tail = lower index, head)
+    std::vector<int32_t> edge_tag;     // N1: 0 interior or PIC_BC_*
+    std::vector<int32_t> edge_face;    // N1 x 2 faces (or -1)
+    std::vector<int8_t> edge_face_sign;// N1 x 2: D_curl entry of (face, edge)
+    std::vector<double> area;          // N2
+    std::vector<double> grad;          // N2 x 3 x 2: grad(lambda_k) (d/dz, d/drho)
+    std::vector<double> mu_inv;        // N2: diagonal of star_mu^-1
+    std::vector<int64_t> eps_ptr;      // star_eps in CSR, N1 rows
+    std::vector<int32_t> eps_idx;
+    std::vector<double> eps_val;
+    std::vector<int32_t> free_edges;   // non-PEC edges, ascending
+    std::vector<int32_t> free_of_edge; // N1: index in free_edges or -1
+    std::vector<uint8_t> node_on_pec;  // N0
+    bool have_spai = false;
+    std::vector<int64_t> M_ptr;        // SPAI M in CSR over free edges
+    std::vector<int32_t> M_idx;
+    std::vector<double> M_val;
+    double dt_stable = 0.0;
+    double lambda_max = 0.0;
+    // uniform bucket grid over triangle bounding boxes, for point location
+    double bb_z0 = 0, bb_r0 = 0, bb_h = 1;
+    int64_t bb_nz = 0, bb_nr = 0;
+    std::vector<int64_t> bb_ptr;
+    std::vector<int32_t> bb_tri;
+};
+
+// local edge k joins local nodes (k+1)%3 and (k+2)%3; its tail is the lower node index
+inline void edge_tail_head(const int32_t *n3, int k, int *a, int *b) {
+    int i = (k + 1) % 3, j = (k + 2) % 3;
+    if (n3[i] < n3[j]) { *a = i; *b = j; } else { *a = j; *b = i; }
+}
+
+// run f(begin, end) over [0, n) on the host's cores
+template <class F>
+void parallel_for(int64_t n, F &&f) {
+    unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    if (n < 4096 || nt == 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    int64_t chunk = (n + nt - 1) / nt;
+    for (unsigned i = 0; i < nt; i++) {
+        int64_t a = (int64_t)i * chunk, b = std::min(n, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([=, &f] { f(a, b); });
+    }
+    for (auto &t : th) t.join();
+}
+
+void build_locator(HostMesh &m);
+// containing triangle (largest smallest barycentric coordinate) or -1; lam[3] out
+int32_t locate_point(const HostMesh &m, double z, double rho, double lam[3]);
+
+// ---------------------------------------------------------------------------------
+// device layouts
+// ---------------------------------------------------------------------------------
+// One record per triangle, read by the particle kernel: static geometry and topology,
+// plus the per-step field coefficients written by the field kernel.  The E field inside
+// the triangle is linear in lambda: E(lambda) = sum_k lambda_k c_k (components z, rho);
+// bphi = (B^{n+1/2} + B^{n-1/2}) / (2 A) is the time-centred B_phi (W2 = 1/A).
+template <class R>
+struct alignas(sizeof(R) == 4 ? 128 : 64) TriRec {
+    R g[4];       // grad lambda_0 (z, rho), grad lambda_1 (z, rho); grad lambda_2 = -g0 - g1
+    R rho[3];     // node rho
+    R inv_area;
+    R c[6];       // c_0 (z, rho), c_1, c_2
+    R bphi;
+    R pad;
+    int32_t node[3];
+    int32_t flags; // bit k: local edge k runs (k+1)%3 -> (k+2)%3 (D_curl entry +1)
+    int32_t edge[3];
+    int32_t pad2;
+    int32_t nbr[3]; // neighbour triangle, or -(PIC_BC_* tag) on the boundary
+    int32_t pad3;
+};
+
+struct PF32 {
+    using R = float;
+    using Lam = int32_t;
+    using Acc = unsigned long long;  // two's-complement int64 accumulators
+    static constexpr bool fixed = true;
+};
+struct PF64 {
+    using R = double;
+    using Lam = double;
+    using Acc = double;
+    static constexpr bool fixed = false;
+};
+
+template <class P>
+struct Particles {
+    int32_t *tri = nullptr;
+    typename P::Lam *l0 = nullptr, *l1 = nullptr;
+    typename P::R *ur = nullptr, *up = nullptr, *uz = nullptr;
+    int32_t *pid = nullptr;
+};
+
+enum { CNT_ABSORBED = 0, CNT_OVERFLOW = 1, CNT_CROSSINGS = 2, CNT_N = 4 };
+
+template <class P>
+struct PushArgs {
+    const TriRec<typename P::R> *rec;
+    Particles<P> p;
+    const int64_t *n_slots;     // device count of slots
+    typename P::Acc *J;         // N1, units: fixed 2^-44 (FP32) / 1 (FP64) of q_src/dt
+    typename P::Acc *Q;         // N0, Q^{n+1}, units 2^-22 / 1 of q_src
+    typename P::Acc *Qabs;      // N0
+    unsigned long long *counters;
+    typename P::R qmdt2;        // q dt / (2 m)
+    typename P::R dt;
+    typename P::R inv_c2;
+    typename P::R bz;
+    int32_t walk_cap;
+};
+
+template <class P>
+struct FieldArgs {
+    TriRec<typename P::R> *rec;
+    typename P::R *E;           // N1
+    typename P::R *B;           // N2, B^{n-1/2} in, B^{n+1/2} out
+    const typename P::R *mu_inv;// N2
+    const int32_t *edge_face;   // N1 x 2: (face+1) * sign, 0 if none
+    const int32_t *free_edges;  // nf
+    const typename P::Acc *J;   // N1
+    double *D;                  // N1 auxiliary dual flux (DGL)
+    typename P::R *r;           // nf scratch: D_curl^T star_mu^-1 B - J
+    // M in sliced ELL: slices of 32 rows, column-major inside a slice
+    const int64_t *ell_off;     // n_slices + 1, element offset of each slice
+    const int32_t *ell_col;
+    const typename P::R *ell_val;
+    int64_t N1, N2, nf;
+    typename P::R dt;
+    double j_scale;             // physical J = J_acc * j_scale
+};
+
+template <class P> void launch_push(const PushArgs<P> &a, int64_t n_bound, cudaStream_t s);
+template <class P> void launch_field_b(const FieldArgs<P> &a, cudaStream_t s);
+template <class P> void launch_field_e(const FieldArgs<P> &a, cudaStream_t s);
+template <class P>
+void launch_deposit_q(const TriRec<typename P::R> *rec, Particles<P> p, int64_t first,
+                      int64_t count, typename P::Acc *Q, cudaStream_t s);
+
+struct SortScratch {
+    int32_t *cnt = nullptr;      // N2 + 1: counts, then write cursors
+    int32_t *blk = nullptr;      // scan chunk sums
+    int64_t *n_old = nullptr;    // slot count before the sort
+};
+// stable-enough counting sort by triangle; drops removed particles; writes the new
+// slot count to *n_slots (device)
+template <class P>
+void launch_resort(Particles<P> src, Particles<P> dst, int64_t *n_slots, int64_t n_bound,
+                   int64_t N2, const SortScratch &sc, cudaStream_t s);
+
+// diagnostics, FP64 reductions on the device
+struct DiagDev {
+    const int64_t *node_ptr;     // N0 + 1: node -> incident edges (CSR)
+    const int32_t *node_edge;    // incident edge
+    const int8_t *node_sign;     // D_div entry: +1 tail, -1 head
+    const uint8_t *node_on_pec;  // N0
+    const int64_t *eps_ptr;      // star_eps CSR
+    const int32_t *eps_idx;
+    const double *eps_val;
+    int64_t N0, N1, N2;
+};
+// out[0]: max |dce| (units of q_src), out[1]: count of nonzero dce (fixed: exact),
+// out[2]: max |NR_DCE|, out[3]: max |dgl - ref|, out[4]: max |Q|, out[5]: field energy,
+// out[6]: sum (gamma - 1) over live particles
+template <class P>
+void launch_diag(const DiagDev &d, const typename P::Acc *J, const typename P::Acc *Qn,
+                 const typename P::Acc *Qp, const typename P::Acc *Qabs, const double *D,
+                 double *dgl_ref, int set_ref, const typename P::R *E,
+                 const typename P::R *B, const typename P::R *mu_inv, Particles<P> p,
+                 const int64_t *n_slots, int64_t n_bound, double q_scale, double inv_c2,
+                 double *out, cudaStream_t s);
+template <class P>
+void launch_export(Particles<P> p, int64_t n, const TriRec<typename P::R> *rec,
+                   double *lam3, double *u3, int64_t *pid, cudaStream_t s);
+template <class P>
+void launch_acc_to_double(const typename P::Acc *a, double *out, int64_t n, double scale,
+                          cudaStream_t s);
+
+}  // namespace pic
+
+struct pic_mesh {
+    pic::HostMesh h;
+};

@@ -1,0 +1,810 @@
+// Simulation object: device-resident fields, operators and particles, and the per-step
+// launch sequence of the paper's cycle (Sec. 3).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+struct Allocator {
+    pic_alloc_fn alloc = nullptr;
+    pic_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+static Allocator g_allocator;
+static std::mutex g_allocator_mu;
+
+struct SimBase {
+    virtual ~SimBase() = default;
+    virtual pic_status fields_set(const double *E, const double *B, cudaStream_t s) = 0;
+    virtual pic_status inject(int64_t n, const double *z, const double *rho, const double *ur,
+                              const double *up, const double *uz, double q, double m, double w,
+                              cudaStream_t s) = 0;
+    virtual pic_status step(int64_t n, cudaStream_t s) = 0;
+    virtual pic_status diagnostics(pic_diag *o, double *E, double *B, double *J,
+                                   cudaStream_t s) = 0;
+    virtual pic_status charges(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
+    virtual pic_status count(int64_t *n, cudaStream_t s) = 0;
+    virtual pic_status get(int64_t cap, int64_t *pid, int32_t *tri, double *lam, double *u,
+                           cudaStream_t s) = 0;
+    virtual int64_t raw_bytes() const = 0;
+    virtual pic_status raw_get(void *dst, int64_t n, cudaStream_t s) = 0;
+    virtual pic_status raw_set(const void *src, int64_t n, cudaStream_t s) = 0;
+    virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
+    int32_t sort_interval = 4;
+    int device = 0;
+};
+
+template <class P>
+struct SimImpl final : SimBase {
+    using R = typename P::R;
+    using Acc = typename P::Acc;
+    using Lam = typename P::Lam;
+
+    const HostMesh *m = nullptr;
+    Allocator al;
+    std::vector<void *> allocs;
+    double dt = 0, bz = 0, q = 0, mass = 0, weight = 0, q_src = 0, qm = 0;
+    bool have_species = false;
+    int64_t cap = 0, n_bound = 0, next_pid = 0, n_steps = 0, n_injected = 0;
+    int cur = 0, qcur = 0, since_sort = 0;
+    bool dgl_dirty = true;
+    int64_t nf = 0, n_slices = 0;
+
+    TriRec<R> *rec = nullptr;
+    R *E = nullptr, *B = nullptr, *mu_inv = nullptr, *r = nullptr;
+    int32_t *edge_face = nullptr, *free_edges = nullptr;
+    double *D = nullptr;
+    int64_t *ell_off = nullptr;
+    int32_t *ell_col = nullptr;
+    R *ell_val = nullptr;
+    Acc *J = nullptr, *Qbuf[2] = {nullptr, nullptr}, *Qabs = nullptr;
+    Particles<P> parts[2];
+    int64_t *d_n = nullptr;
+    unsigned long long *counters = nullptr;
+    SortScratch sc;
+    DiagDev dd{};
+    double *dgl_ref = nullptr, *diag_out = nullptr;
+
+    bool timing_on = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+
+    ~SimImpl() override {
+        cudaSetDevice(device);
+        cudaDeviceSynchronize();
+        for (auto &e : ev_pending) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        for (auto e : ev_free) cudaEventDestroy(e);
+        for (void *p : allocs) {
+            if (al.free) al.free(p, al.ctx);
+            else cudaFree(p);
+        }
+    }
+
+    template <class T>
+    pic_status dalloc(T *&p, int64_t n) {
+        size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(n, 1);
+        void *v = nullptr;
+        if (al.alloc) {
+            v = al.alloc(bytes, al.ctx);
+            if (!v) {
+                set_error("device allocation of %zu bytes failed", bytes);
+                return PIC_ERR_OOM;
+            }
+        } else {
+            cudaError_t e = cudaMalloc(&v, bytes);
+            if (e != cudaSuccess) {
+                set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+                return e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA;
+            }
+        }
+        allocs.push_back(v);
+        p = static_cast<T *>(v);
+        return PIC_OK;
+    }
+
+    template <class T>
+    pic_status upload(T *&p, const std::vector<T> &h) {
+        pic_status st = dalloc(p, (int64_t)h.size());
+        if (st != PIC_OK) return st;
+        if (!h.empty()) PIC_CUDA_TRY(cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+        return PIC_OK;
+    }
+
+    pic_status init(const HostMesh &mesh, double dt_, double bz_, int64_t cap_) {
+        m = &mesh;
+        dt = dt_;
+        bz = bz_;
+        cap = cap_;
+        nf = (int64_t)mesh.free_edges.size();
+        PIC_CUDA_TRY(cudaGetDevice(&device));
+        pic_status st;
+        // triangle records
+        std::vector<TriRec<R>> hr(mesh.N2);
+        for (int64_t t = 0; t < mesh.N2; t++) {
+            TriRec<R> &x = hr[t];
+            std::memset(&x, 0, sizeof x);
+            for (int k = 0; k < 4; k++) x.g[k] = (R)mesh.grad[6 * t + k];
+            int flags = 0;
+            for (int k = 0; k < 3; k++) {
+                int32_t nk = mesh.tri[3 * t + k];
+                x.node[k] = nk;
+                x.rho[k] = (R)mesh.zr[2 * nk + 1];
+                x.edge[k] = mesh.tri_edge[3 * t + k];
+                int32_t nb = mesh.tri_nbr[3 * t + k];
+                x.nbr[k] = nb >= 0 ? nb : -mesh.edge_tag[mesh.tri_edge[3 * t + k]];
+                if (mesh.tri[3 * t + (k + 1) % 3] < mesh.tri[3 * t + (k + 2) % 3]) flags |= 1 << k;
+            }
+            x.flags = flags;
+            x.inv_area = (R)(1.0 / mesh.area[t]);
+        }
+        if ((st = upload(rec, hr)) != PIC_OK) return st;
+        std::vector<R> hmu(mesh.mu_inv.begin(), mesh.mu_inv.end());
+        if ((st = upload(mu_inv, hmu)) != PIC_OK) return st;
+        std::vector<int32_t> hef(2 * mesh.N1, 0);
+        for (int64_t e = 0; e < mesh.N1; e++)
+            for (int q2 = 0; q2 < 2; q2++) {
+                int32_t f = mesh.edge_face[2 * e + q2];
+                if (f >= 0) hef[2 * e + q2] = (f + 1) * mesh.edge_face_sign[2 * e + q2];
+            }
+        if ((st = upload(edge_face, hef)) != PIC_OK) return st;
+        if ((st = upload(free_edges, mesh.free_edges)) != PIC_OK) return st;
+        // M as sliced ELL (slices of 32 rows, column-major inside a slice)
+        n_slices = (nf + 31) / 32;
+        std::vector<int64_t> hoff(n_slices + 1, 0);
+        for (int64_t sl = 0; sl < n_slices; sl++) {
+            int64_t w = 0;
+            for (int64_t i = sl * 32; i < std::min(nf, sl * 32 + 32); i++)
+                w = std::max<int64_t>(w, mesh.M_ptr[i + 1] - mesh.M_ptr[i]);
+            hoff[sl + 1] = hoff[sl] + 32 * w;
+        }
+        std::vector<int32_t> hcol(std::max<int64_t>(hoff[n_slices], 1), 0);
+        std::vector<R> hval(std::max<int64_t>(hoff[n_slices], 1), R(0));
+        for (int64_t i = 0; i < nf; i++) {
+            int64_t sl = i / 32, lane = i % 32, k = 0;
+            for (int64_t q2 = mesh.M_ptr[i]; q2 < mesh.M_ptr[i + 1]; q2++, k++) {
+                hcol[hoff[sl] + 32 * k + lane] = mesh.M_idx[q2];
+                hval[hoff[sl] + 32 * k + lane] = (R)mesh.M_val[q2];
+            }
+        }
+        if ((st = upload(ell_off, hoff)) != PIC_OK) return st;
+        if ((st = upload(ell_col, hcol)) != PIC_OK) return st;
+        if ((st = upload(ell_val, hval)) != PIC_OK) return st;
+        // fields and accumulators
+        if ((st = dalloc(E, mesh.N1)) || (st = dalloc(B, mesh.N2)) || (st = dalloc(D, mesh.N1)) ||
+            (st = dalloc(r, nf)) || (st = dalloc(J, mesh.N1)) || (st = dalloc(Qbuf[0], mesh.N0)) ||
+            (st = dalloc(Qbuf[1], mesh.N0)) || (st = dalloc(Qabs, mesh.N0)))
+            return st;
+        PIC_CUDA_TRY(cudaMemset(E, 0, sizeof(R) * mesh.N1));
+        PIC_CUDA_TRY(cudaMemset(B, 0, sizeof(R) * mesh.N2));
+        PIC_CUDA_TRY(cudaMemset(D, 0, sizeof(double) * mesh.N1));
+        PIC_CUDA_TRY(cudaMemset(J, 0, sizeof(Acc) * mesh.N1));
+        for (int k = 0; k < 2; k++) PIC_CUDA_TRY(cudaMemset(Qbuf[k], 0, sizeof(Acc) * mesh.N0));
+        PIC_CUDA_TRY(cudaMemset(Qabs, 0, sizeof(Acc) * mesh.N0));
+        // particles, double-buffered for the re-sort
+        for (int k = 0; k < 2; k++) {
+            Particles<P> &p = parts[k];
+            if ((st = dalloc(p.tri, cap)) || (st = dalloc(p.l0, cap)) || (st = dalloc(p.l1, cap)) ||
+                (st = dalloc(p.ur, cap)) || (st = dalloc(p.up, cap)) || (st = dalloc(p.uz, cap)) ||
+                (st = dalloc(p.pid, cap)))
+                return st;
+        }
+        if ((st = dalloc(d_n, 1)) || (st = dalloc(counters, CNT_N))) return st;
+        PIC_CUDA_TRY(cudaMemset(d_n, 0, sizeof(int64_t)));
+        PIC_CUDA_TRY(cudaMemset(counters, 0, sizeof(unsigned long long) * CNT_N));
+        // sort scratch
+        if ((st = dalloc(sc.cnt, mesh.N2 + 1)) || (st = dalloc(sc.blk, mesh.N2 / 2048 + 2)) ||
+            (st = dalloc(sc.n_old, 1)))
+            return st;
+        // diagnostics: node -> edge incidence (D_div rows), star_eps
+        std::vector<int64_t> nptr(mesh.N0 + 1, 0);
+        for (int64_t e = 0; e < mesh.N1; e++) {
+            nptr[mesh.edge_nodes[2 * e] + 1]++;
+            nptr[mesh.edge_nodes[2 * e + 1] + 1]++;
+        }
+        for (int64_t k = 0; k < mesh.N0; k++) nptr[k + 1] += nptr[k];
+        std::vector<int32_t> nedge(nptr[mesh.N0]);
+        std::vector<int8_t> nsign(nptr[mesh.N0]);
+        std::vector<int64_t> fill(nptr.begin(), nptr.end() - 1);
+        for (int64_t e = 0; e < mesh.N1; e++) {
+            int32_t a = mesh.edge_nodes[2 * e], b = mesh.edge_nodes[2 * e + 1];
+            nedge[fill[a]] = (int32_t)e;
+            nsign[fill[a]++] = 1;   // current leaves the tail
+            nedge[fill[b]] = (int32_t)e;
+            nsign[fill[b]++] = -1;
+        }
+        int64_t *np_ = nullptr, *ep_ = nullptr;
+        int32_t *ne_ = nullptr, *ei_ = nullptr;
+        int8_t *ns_ = nullptr;
+        uint8_t *pec_ = nullptr;
+        double *ev_ = nullptr;
+        std::vector<int64_t> eptr(mesh.eps_ptr.begin(), mesh.eps_ptr.end());
+        if ((st = upload(np_, nptr)) || (st = upload(ne_, nedge)) || (st = upload(ns_, nsign)) ||
+            (st = upload(pec_, mesh.node_on_pec)) || (st = upload(ep_, eptr)) ||
+            (st = upload(ei_, mesh.eps_idx)) || (st = upload(ev_, mesh.eps_val)))
+            return st;
+        dd = DiagDev{np_, ne_, ns_, pec_, ep_, ei_, ev_, mesh.N0, mesh.N1, mesh.N2};
+        if ((st = dalloc(dgl_ref, mesh.N0)) || (st = dalloc(diag_out, 8))) return st;
+        PIC_CUDA_TRY(cudaDeviceSynchronize());
+        return PIC_OK;
+    }
+
+    Acc *Qn() { return Qbuf[qcur]; }
+    double j_scale() const { return (P::fixed ? J_INV : 1.0) * q_src / dt; }
+    double q_scale() const { return q_src; }
+
+    FieldArgs<P> field_args() {
+        FieldArgs<P> a;
+        a.rec = rec;
+        a.E = E;
+        a.B = B;
+        a.mu_inv = mu_inv;
+        a.edge_face = edge_face;
+        a.free_edges = free_edges;
+        a.J = J;
+        a.D = D;
+        a.r = r;
+        a.ell_off = ell_off;
+        a.ell_col = ell_col;
+        a.ell_val = ell_val;
+        a.N1 = m->N1;
+        a.N2 = m->N2;
+        a.nf = nf;
+        a.dt = (R)dt;
+        a.j_scale = j_scale();
+        return a;
+    }
+
+    pic_status fields_set(const double *Eh, const double *Bh, cudaStream_t s) override {
+        if (Eh) {
+            std::vector<R> e(m->N1);
+            std::vector<double> ed(m->N1);
+            for (int64_t i = 0; i < m->N1; i++) {
+                double v = m->edge_tag[i] == PIC_BC_PEC ? 0.0 : Eh[i];
+                ed[i] = v;
+                e[i] = (R)v;
+            }
+            // auxiliary dual flux D = star_eps E (Sec. 3.5.2)
+            std::vector<double> dh(m->N1, 0.0);
+            for (int64_t i = 0; i < m->N1; i++) {
+                double acc = 0;
+                for (int64_t k = m->eps_ptr[i]; k < m->eps_ptr[i + 1]; k++)
+                    acc += m->eps_val[k] * (double)e[m->eps_idx[k]];
+                dh[i] = acc;
+            }
+            PIC_CUDA_TRY(cudaMemcpyAsync(E, e.data(), sizeof(R) * m->N1, cudaMemcpyHostToDevice, s));
+            PIC_CUDA_TRY(cudaMemcpyAsync(D, dh.data(), sizeof(double) * m->N1, cudaMemcpyHostToDevice, s));
+            PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        if (Bh) {
+            std::vector<R> b(Bh, Bh + m->N2);
+            PIC_CUDA_TRY(cudaMemcpyAsync(B, b.data(), sizeof(R) * m->N2, cudaMemcpyHostToDevice, s));
+            PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        dgl_dirty = true;
+        return PIC_OK;
+    }
+
+    pic_status read_count(int64_t *n, cudaStream_t s) {
+        PIC_CUDA_TRY(cudaMemcpyAsync(n, d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        return PIC_OK;
+    }
+
+    pic_status resort(cudaStream_t s) {
+        launch_resort<P>(parts[cur], parts[1 - cur], d_n, n_bound, m->N2, sc, s);
+        cur = 1 - cur;
+        since_sort = 0;
+        return PIC_OK;
+    }
+
+    pic_status inject(int64_t n, const double *z, const double *rho, const double *ur,
+                      const double *up, const double *uz, double q_, double m_, double w_,
+                      cudaStream_t s) override {
+        if (n < 0 || (n > 0 && (!z || !rho || !ur || !up || !uz)) || !(m_ > 0) || !(w_ > 0) ||
+            !std::isfinite(q_)) {
+            set_error("pic_particles_inject: bad argument");
+            return PIC_ERR_ARG;
+        }
+        double qsrc = w_ * q_ / (2.0 * M_PI);
+        if (have_species && (q_ / m_ != qm || qsrc != q_src)) {
+            set_error("pic_particles_inject: one species per simulation (q/m and q*w must match)");
+            return PIC_ERR_ARG;
+        }
+        if (n == 0) return PIC_OK;
+        int64_t n_now = 0;
+        pic_status st = read_count(&n_now, s);
+        if (st != PIC_OK) return st;
+        if (n_now + n > cap) {
+            set_error("pic_particles_inject: capacity %lld exceeded", (long long)cap);
+            return PIC_ERR_OOM;
+        }
+        std::vector<int32_t> tri(n), pid(n);
+        std::vector<Lam> l0(n), l1(n);
+        std::vector<R> vr(n), vp(n), vz(n);
+        std::vector<uint8_t> bad(1, 0);
+        const HostMesh &mm = *m;
+        parallel_for(n, [&](int64_t a, int64_t b) {
+            for (int64_t i = a; i < b; i++) {
+                double lam[3];
+                int32_t t = locate_point(mm, z[i], rho[i], lam);
+                if (t < 0 || !std::isfinite(ur[i] + up[i] + uz[i])) {
+                    bad[0] = 1;
+                    continue;
+                }
+                tri[i] = t;
+                if constexpr (P::fixed) {
+                    // integers that sum to 2^22
+                    double a0 = std::max(lam[0], 0.0), a1 = std::max(lam[1], 0.0),
+                           a2 = std::max(lam[2], 0.0);
+                    double ss = a0 + a1 + a2;
+                    int32_t q0 = (int32_t)std::nearbyint(a0 / ss * LAM_ONE);
+                    int32_t q1 = (int32_t)std::nearbyint(a1 / ss * LAM_ONE);
+                    int32_t q2 = LAM_ONE - q0 - q1;
+                    if (q2 < 0) {
+                        if (q0 >= q1) q0 += q2; else q1 += q2;
+                    }
+                    l0[i] = q0;
+                    l1[i] = q1;
+                } else {
+                    l0[i] = lam[0];
+                    l1[i] = lam[1];
+                }
+                vr[i] = (R)ur[i];
+                vp[i] = (R)up[i];
+                vz[i] = (R)uz[i];
+                pid[i] = (int32_t)(next_pid + i);
+            }
+        });
+        if (bad[0]) {
+            set_error("pic_particles_inject: a particle lies outside the mesh or is not finite");
+            return PIC_ERR_ARG;
+        }
+        if (!have_species) {
+            have_species = true;
+            q = q_;
+            mass = m_;
+            weight = w_;
+            qm = q_ / m_;
+            q_src = qsrc;
+        }
+        Particles<P> &p = parts[cur];
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.tri + n_now, tri.data(), 4 * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.l0 + n_now, l0.data(), sizeof(Lam) * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.l1 + n_now, l1.data(), sizeof(Lam) * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.ur + n_now, vr.data(), sizeof(R) * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.up + n_now, vp.data(), sizeof(R) * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.uz + n_now, vz.data(), sizeof(R) * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.pid + n_now, pid.data(), 4 * n, cudaMemcpyHostToDevice, s));
+        int64_t n_new = n_now + n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n_new, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        launch_deposit_q<P>(rec, p, n_now, n, Qn(), s);
+        n_bound = n_new;
+        next_pid += n;
+        n_injected += n;
+        resort(s);
+        PIC_CUDA_TRY(cudaGetLastError());
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        dgl_dirty = true;
+        return PIC_OK;
+    }
+
+    pic_status step(int64_t n, cudaStream_t s) override {
+        if (n < 0) {
+            set_error("pic_step: negative step count");
+            return PIC_ERR_ARG;
+        }
+        FieldArgs<P> fa = field_args();
+        for (int64_t it = 0; it < n; it++) {
+            if (dgl_dirty) {
+                // DGL reference res = D_div D^n - Q^n before the first step of this state
+                launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, D, dgl_ref, 1, E, B, mu_inv,
+                               parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
+                dgl_dirty = false;
+            }
+            Acc *Qnext = Qbuf[1 - qcur];
+            PIC_CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(Acc) * m->N1, s));
+            PIC_CUDA_TRY(cudaMemsetAsync(Qnext, 0, sizeof(Acc) * m->N0, s));
+            PIC_CUDA_TRY(cudaMemsetAsync(Qabs, 0, sizeof(Acc) * m->N0, s));
+            launch_field_b<P>(fa, s);
+            PushArgs<P> pa;
+            pa.rec = rec;
+            pa.p = parts[cur];
+            pa.n_slots = d_n;
+            pa.J = J;
+            pa.Q = Qnext;
+            pa.Qabs = Qabs;
+            pa.counters = counters;
+            pa.qmdt2 = (R)(0.5 * qm * dt);
+            pa.dt = (R)dt;
+            pa.inv_c2 = (R)(1.0 / (m->units.c * m->units.c));
+            pa.bz = (R)bz;
+            pa.walk_cap = m->units.walk_cap;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (timing_on) {
+                e0 = take_event();
+                e1 = take_event();
+                cudaEventRecord(e0, s);
+            }
+            launch_push<P>(pa, n_bound, s);
+            if (timing_on) {
+                cudaEventRecord(e1, s);
+                ev_pending.push_back({e0, e1});
+            }
+            launch_field_e<P>(fa, s);
+            qcur = 1 - qcur;
+            n_steps++;
+            if (sort_interval > 0 && ++since_sort >= sort_interval) resort(s);
+        }
+        PIC_CUDA_TRY(cudaGetLastError());
+        return PIC_OK;
+    }
+
+    cudaEvent_t take_event() {
+        if (!ev_free.empty()) {
+            cudaEvent_t e = ev_free.back();
+            ev_free.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+
+    pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) override {
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        double tot = 0;
+        for (auto &pr : ev_pending) {
+            float x = 0;
+            PIC_CUDA_TRY(cudaEventElapsedTime(&x, pr.first, pr.second));
+            tot += x;
+            ev_free.push_back(pr.first);
+            ev_free.push_back(pr.second);
+        }
+        if (ms) *ms = tot;
+        if (launches) *launches = (int64_t)ev_pending.size();
+        ev_pending.clear();
+        timing_on = enable != 0;
+        return PIC_OK;
+    }
+
+    pic_status diagnostics(pic_diag *o, double *Eo, double *Bo, double *Jo, cudaStream_t s) override {
+        if (dgl_dirty) {
+            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, D, dgl_ref, 1, E, B, mu_inv,
+                           parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
+            dgl_dirty = false;
+        }
+        double out[8] = {0};
+        unsigned long long cnt[CNT_N] = {0};
+        if (o) {
+            PIC_CUDA_TRY(cudaMemsetAsync(diag_out, 0, sizeof(double) * 8, s));
+            double inv_c2 = 1.0 / (m->units.c * m->units.c);
+            // the last step wrote Q^{n+1} into Qn() and kept Q^n in the other buffer
+            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, D, dgl_ref, 0, E, B, mu_inv,
+                           parts[cur], d_n, n_bound, q_scale(), inv_c2, diag_out, s);
+            PIC_CUDA_TRY(cudaGetLastError());
+            PIC_CUDA_TRY(cudaMemcpyAsync(out, diag_out, sizeof out, cudaMemcpyDeviceToHost, s));
+            PIC_CUDA_TRY(cudaMemcpyAsync(cnt, counters, sizeof cnt, cudaMemcpyDeviceToHost, s));
+        }
+        std::vector<R> eh, bh;
+        std::vector<double> jd;
+        double *jdev = nullptr;
+        if (Eo) {
+            eh.resize(m->N1);
+            PIC_CUDA_TRY(cudaMemcpyAsync(eh.data(), E, sizeof(R) * m->N1, cudaMemcpyDeviceToHost, s));
+        }
+        if (Bo) {
+            bh.resize(m->N2);
+            PIC_CUDA_TRY(cudaMemcpyAsync(bh.data(), B, sizeof(R) * m->N2, cudaMemcpyDeviceToHost, s));
+        }
+        if (Jo) {
+            pic_status st = dalloc(jdev, m->N1);
+            if (st != PIC_OK) return st;
+            launch_acc_to_double<P>(J, jdev, m->N1, j_scale(), s);
+            jd.resize(m->N1);
+            PIC_CUDA_TRY(cudaMemcpyAsync(jd.data(), jdev, sizeof(double) * m->N1, cudaMemcpyDeviceToHost, s));
+        }
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (jdev) release(jdev);
+        if (o) {
+            o->n_absorbed = (int64_t)cnt[CNT_ABSORBED];
+            o->walk_overflows = (int64_t)cnt[CNT_OVERFLOW];
+            o->n_crossings = (int64_t)cnt[CNT_CROSSINGS];
+            o->n_particles = n_injected - (int64_t)cnt[CNT_ABSORBED];
+            o->n_steps = n_steps;
+            o->dce_max = out[0];
+            o->dce_nonzero = (int64_t)out[1];
+            o->nr_dce_max = out[2];
+            o->dgl_drift = out[3] / (out[4] > 0 ? out[4] : 1.0);
+            o->field_energy = out[5];
+            o->kinetic_energy = out[6] * mass * weight * m->units.c * m->units.c;
+            o->q_absorbed = (double)cnt[CNT_ABSORBED] * q * weight;
+        }
+        if (Eo)
+            for (int64_t i = 0; i < m->N1; i++) Eo[i] = (double)eh[i];
+        if (Bo)
+            for (int64_t i = 0; i < m->N2; i++) Bo[i] = (double)bh[i];
+        if (Jo) std::copy(jd.begin(), jd.end(), Jo);
+        return PIC_OK;
+    }
+
+    void release(void *p) {
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) allocs.erase(it);
+        if (al.free) al.free(p, al.ctx);
+        else cudaFree(p);
+    }
+
+    pic_status charges(double *Qo, double *Qpo, double *Qao, cudaStream_t s) override {
+        double *tmp = nullptr;
+        pic_status st = dalloc(tmp, 3 * m->N0);
+        if (st != PIC_OK) return st;
+        double sc_ = (P::fixed ? LAM_INV : 1.0) * q_src;
+        launch_acc_to_double<P>(Qn(), tmp, m->N0, sc_, s);
+        launch_acc_to_double<P>(Qbuf[1 - qcur], tmp + m->N0, m->N0, sc_, s);
+        launch_acc_to_double<P>(Qabs, tmp + 2 * m->N0, m->N0, sc_, s);
+        std::vector<double> h(3 * m->N0);
+        cudaError_t e = cudaMemcpyAsync(h.data(), tmp, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        release(tmp);
+        if (e != cudaSuccess) {
+            set_error("pic_charges_get: %s", cudaGetErrorString(e));
+            return PIC_ERR_CUDA;
+        }
+        if (Qo) std::copy(h.begin(), h.begin() + m->N0, Qo);
+        if (Qpo) std::copy(h.begin() + m->N0, h.begin() + 2 * m->N0, Qpo);
+        if (Qao) std::copy(h.begin() + 2 * m->N0, h.end(), Qao);
+        return PIC_OK;
+    }
+
+    pic_status count(int64_t *n, cudaStream_t s) override {
+        pic_status st = read_count(n, s);
+        if (st == PIC_OK) n_bound = std::min(n_bound, *n);
+        return st;
+    }
+
+    pic_status get(int64_t cap_out, int64_t *pid, int32_t *tri, double *lam, double *u,
+                   cudaStream_t s) override {
+        int64_t n = 0;
+        pic_status st = read_count(&n, s);
+        if (st != PIC_OK) return st;
+        if (n > cap_out) {
+            set_error("pic_particles_get: %lld slots exceed the output capacity", (long long)n);
+            return PIC_ERR_ARG;
+        }
+        if (n == 0) return PIC_OK;
+        double *lam_d = nullptr, *u_d = nullptr;
+        int64_t *pid_d = nullptr;
+        if ((st = dalloc(lam_d, 3 * n)) || (st = dalloc(u_d, 3 * n)) || (st = dalloc(pid_d, n))) return st;
+        launch_export<P>(parts[cur], n, rec, lam_d, u_d, pid_d, s);
+        std::vector<double> hl(3 * n), hu(3 * n);
+        std::vector<int64_t> hp(n);
+        std::vector<int32_t> ht(n);
+        cudaMemcpyAsync(hl.data(), lam_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hu.data(), u_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hp.data(), pid_d, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(ht.data(), parts[cur].tri, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        release(lam_d);
+        release(u_d);
+        release(pid_d);
+        if (e != cudaSuccess) {
+            set_error("pic_particles_get: %s", cudaGetErrorString(e));
+            return PIC_ERR_CUDA;
+        }
+        if (pid) std::copy(hp.begin(), hp.end(), pid);
+        if (tri) std::copy(ht.begin(), ht.end(), tri);
+        if (lam) std::copy(hl.begin(), hl.end(), lam);
+        if (u) std::copy(hu.begin(), hu.end(), u);
+        return PIC_OK;
+    }
+
+    int64_t raw_bytes() const override { return 4 + 2 * (int64_t)sizeof(Lam) + 3 * (int64_t)sizeof(R); }
+
+    pic_status raw_get(void *dst, int64_t n, cudaStream_t s) override {
+        if (!dst || n < 0 || n > cap) {
+            set_error("pic_particles_raw_get: bad argument");
+            return PIC_ERR_ARG;
+        }
+        char *h = static_cast<char *>(dst);
+        const Particles<P> &p = parts[cur];
+        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.tri, 4 * n, cudaMemcpyDeviceToHost, s));
+        h += 4 * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.l0, sizeof(Lam) * n, cudaMemcpyDeviceToHost, s));
+        h += sizeof(Lam) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.l1, sizeof(Lam) * n, cudaMemcpyDeviceToHost, s));
+        h += sizeof(Lam) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.ur, sizeof(R) * n, cudaMemcpyDeviceToHost, s));
+        h += sizeof(R) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.up, sizeof(R) * n, cudaMemcpyDeviceToHost, s));
+        h += sizeof(R) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.uz, sizeof(R) * n, cudaMemcpyDeviceToHost, s));
+        return PIC_OK;
+    }
+
+    pic_status raw_set(const void *src, int64_t n, cudaStream_t s) override {
+        if (!src || n < 0 || n > cap) {
+            set_error("pic_particles_raw_set: bad argument");
+            return PIC_ERR_ARG;
+        }
+        const char *h = static_cast<const char *>(src);
+        const Particles<P> &p = parts[cur];
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.tri, h, 4 * n, cudaMemcpyHostToDevice, s));
+        h += 4 * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.l0, h, sizeof(Lam) * n, cudaMemcpyHostToDevice, s));
+        h += sizeof(Lam) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.l1, h, sizeof(Lam) * n, cudaMemcpyHostToDevice, s));
+        h += sizeof(Lam) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.ur, h, sizeof(R) * n, cudaMemcpyHostToDevice, s));
+        h += sizeof(R) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.up, h, sizeof(R) * n, cudaMemcpyHostToDevice, s));
+        h += sizeof(R) * n;
+        PIC_CUDA_TRY(cudaMemcpyAsync(p.uz, h, sizeof(R) * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        n_bound = n;
+        dgl_dirty = true;
+        return PIC_OK;
+    }
+};
+
+}  // namespace pic
+
+using namespace pic;
+
+struct pic_sim {
+    std::unique_ptr<pic::SimBase> impl;
+};
+
+#define SIM_CHECK(s, name)                                   \
+    do {                                                     \
+        if (!(s) || !(s)->impl) {                            \
+            pic::set_error("%s: null simulation", name);     \
+            return PIC_ERR_ARG;                              \
+        }                                                    \
+        cudaError_t e__ = cudaSetDevice((s)->impl->device);  \
+        if (e__ != cudaSuccess) {                            \
+            pic::set_error("%s: %s", name, cudaGetErrorString(e__)); \
+            return PIC_ERR_CUDA;                             \
+        }                                                    \
+    } while (0)
+
+extern "C" pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_, void *ctx) {
+    if ((alloc == nullptr) != (free_ == nullptr)) {
+        set_error("pic_set_allocator: give both functions or neither");
+        return PIC_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_allocator_mu);
+    g_allocator.alloc = alloc;
+    g_allocator.free = free_;
+    g_allocator.ctx = ctx;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sim_create(pic_mesh *pm, double dt, double bz, int64_t max_particles,
+                                     pic_sim **out) {
+    if (!pm || !out || !(dt > 0) || !std::isfinite(bz) || max_particles < 0 ||
+        max_particles >= ((int64_t)1 << 31)) {
+        set_error("pic_sim_create: bad argument");
+        return PIC_ERR_ARG;
+    }
+    if (!pm->h.have_spai) {
+        set_error("pic_sim_create: call pic_spai_build first");
+        return PIC_ERR_STATE;
+    }
+    if (dt > pm->h.dt_stable) {
+        set_error("pic_sim_create: dt %g above the stable limit %g", dt, pm->h.dt_stable);
+        return PIC_ERR_UNSTABLE;
+    }
+    std::unique_ptr<pic_sim> s(new (std::nothrow) pic_sim);
+    if (!s) {
+        set_error("pic_sim_create: out of host memory");
+        return PIC_ERR_OOM;
+    }
+    pic_status st;
+    Allocator al;
+    {
+        std::lock_guard<std::mutex> lk(g_allocator_mu);
+        al = g_allocator;
+    }
+    if (pm->h.units.precision == PIC_FP32) {
+        auto *x = new SimImpl<PF32>;
+        x->al = al;
+        s->impl.reset(x);
+        st = x->init(pm->h, dt, bz, max_particles);
+    } else {
+        auto *x = new SimImpl<PF64>;
+        x->al = al;
+        s->impl.reset(x);
+        st = x->init(pm->h, dt, bz, max_particles);
+    }
+    if (st != PIC_OK) return st;
+    *out = s.release();
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval) {
+    SIM_CHECK(s, "pic_sim_set_sort_interval");
+    if (interval < 0) {
+        set_error("pic_sim_set_sort_interval: negative interval");
+        return PIC_ERR_ARG;
+    }
+    s->impl->sort_interval = interval;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_fields_set(pic_sim *s, const double *E, const double *B, void *st) {
+    SIM_CHECK(s, "pic_fields_set");
+    return s->impl->fields_set(E, B, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_particles_inject(pic_sim *s, int64_t n, const double *z,
+                                           const double *rho, const double *ur, const double *up,
+                                           const double *uz, double q, double m, double w, void *st) {
+    SIM_CHECK(s, "pic_particles_inject");
+    return s->impl->inject(n, z, rho, ur, up, uz, q, m, w, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_step(pic_sim *s, int64_t n, void *st) {
+    SIM_CHECK(s, "pic_step");
+    return s->impl->step(n, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_diagnostics(pic_sim *s, pic_diag *o, double *E, double *B, double *J,
+                                      void *st) {
+    SIM_CHECK(s, "pic_diagnostics");
+    return s->impl->diagnostics(o, E, B, J, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_charges_get(pic_sim *s, double *Q, double *Qp, double *Qa, void *st) {
+    SIM_CHECK(s, "pic_charges_get");
+    return s->impl->charges(Q, Qp, Qa, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_particles_count(pic_sim *s, int64_t *n, void *st) {
+    SIM_CHECK(s, "pic_particles_count");
+    if (!n) {
+        set_error("pic_particles_count: null output");
+        return PIC_ERR_ARG;
+    }
+    return s->impl->count(n, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_particles_get(pic_sim *s, int64_t cap, int64_t *pid, int32_t *tri,
+                                        double *lam, double *u, void *st) {
+    SIM_CHECK(s, "pic_particles_get");
+    return s->impl->get(cap, pid, tri, lam, u, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_particles_raw_bytes(pic_sim *s, int64_t *b) {
+    SIM_CHECK(s, "pic_particles_raw_bytes");
+    if (!b) {
+        set_error("pic_particles_raw_bytes: null output");
+        return PIC_ERR_ARG;
+    }
+    *b = s->impl->raw_bytes();
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_particles_raw_get(pic_sim *s, void *dst, int64_t n, void *st) {
+    SIM_CHECK(s, "pic_particles_raw_get");
+    return s->impl->raw_get(dst, n, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_particles_raw_set(pic_sim *s, const void *src, int64_t n, void *st) {
+    SIM_CHECK(s, "pic_particles_raw_set");
+    return s->impl->raw_set(src, n, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_kernel_timing(pic_sim *s, int32_t enable, double *ms, int64_t *launches,
+                                        void *st) {
+    SIM_CHECK(s, "pic_kernel_timing");
+    return s->impl->timing(enable, ms, launches, (cudaStream_t)st);
+}
+
+extern "C" void pic_sim_destroy(pic_sim *s) { delete s; }

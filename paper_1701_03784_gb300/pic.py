@@ -1,0 +1,358 @@
+"""Thin ctypes binding of the C ABI in include/pic.h (same function names).
+
+Argument marshalling only: every step of the method runs inside libpic_gb300.so.  The
+library must have been built (``paper_1701_03784_gb300._build.build()``); importing this
+module without it raises ImportError -- there is no fallback implementation.
+"""
+import atexit
+import ctypes
+import os
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic_gb300.so")
+
+PIC_OK, PIC_ERR_ARG, PIC_ERR_MESH, PIC_ERR_CUDA, PIC_ERR_UNSTABLE, PIC_ERR_TIMEOUT, \
+    PIC_ERR_OOM, PIC_ERR_STATE = range(8)
+PIC_BC_PEC, PIC_BC_AXIS, PIC_BC_ABSORB = 1, 2, 3
+PIC_FP64, PIC_FP32 = 0, 1
+_STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_MESH", 3: "PIC_ERR_CUDA",
+           4: "PIC_ERR_UNSTABLE", 5: "PIC_ERR_TIMEOUT", 6: "PIC_ERR_OOM", 7: "PIC_ERR_STATE"}
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__("%s: %s (%s)" % (where, msg, _STATUS.get(status, status)))
+        self.status = status
+
+
+class pic_units(ctypes.Structure):
+    _fields_ = [("eps0", ctypes.c_double), ("mu0", ctypes.c_double), ("c", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("walk_cap", ctypes.c_int32)]
+
+
+class pic_diag(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("n_absorbed", ctypes.c_int64),
+                ("walk_overflows", ctypes.c_int64), ("n_crossings", ctypes.c_int64),
+                ("n_steps", ctypes.c_int64), ("dce_max", ctypes.c_double),
+                ("dce_nonzero", ctypes.c_int64), ("nr_dce_max", ctypes.c_double),
+                ("dgl_drift", ctypes.c_double), ("field_energy", ctypes.c_double),
+                ("kinetic_energy", ctypes.c_double), ("q_absorbed", ctypes.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpic_gb300.so is not built; run paper_1701_03784_gb300._build.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_SIGS = {
+    "pic_set_allocator": [_ALLOC_FN, _FREE_FN, _P],
+    "pic_mesh_create": [_P, _I64, _P, _I64, _P, _P, _I64, ctypes.POINTER(pic_units), _P],
+    "pic_mesh_info": [_P, _P, _P, _P, _P, _P],
+    "pic_mesh_edges": [_P, _P],
+    "pic_spai_build": [_P, _I32, _D, _P],
+    "pic_spai_get": [_P, _P, _P, _P, _P],
+    "pic_sim_create": [_P, _D, _D, _I64, _P],
+    "pic_sim_set_sort_interval": [_P, _I32],
+    "pic_fields_set": [_P, _P, _P, _P],
+    "pic_particles_inject": [_P, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _P],
+    "pic_step": [_P, _I64, _P],
+    "pic_diagnostics": [_P, ctypes.POINTER(pic_diag), _P, _P, _P, _P],
+    "pic_charges_get": [_P, _P, _P, _P, _P],
+    "pic_particles_count": [_P, _P, _P],
+    "pic_particles_get": [_P, _I64, _P, _P, _P, _P, _P],
+    "pic_particles_raw_bytes": [_P, _P],
+    "pic_particles_raw_get": [_P, _P, _I64, _P],
+    "pic_particles_raw_set": [_P, _P, _I64, _P],
+    "pic_kernel_timing": [_P, _I32, _P, _P, _P],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.pic_last_error.restype = ctypes.c_char_p
+_lib.pic_last_error.argtypes = []
+_lib.pic_sim_destroy.argtypes = [_P]
+_lib.pic_sim_destroy.restype = None
+_lib.pic_mesh_destroy.argtypes = [_P]
+_lib.pic_mesh_destroy.restype = None
+
+EXPORTED = sorted(list(_SIGS) + ["pic_last_error", "pic_sim_destroy", "pic_mesh_destroy"])
+
+
+def _check(status, where):
+    if status != PIC_OK:
+        raise PicError(status, where, pic_last_error())
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    """CUDA stream handle: an int, a torch.cuda.Stream, or None for torch's current stream
+    (the legacy default stream when torch is absent)."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def pic_last_error():
+    return _lib.pic_last_error().decode()
+
+
+# ---- device memory from PyTorch's caching allocator ------------------------------------
+_torch_hooks = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch.cuda's caching allocator."""
+    global _torch_hooks
+    import torch
+
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
+        except RuntimeError:
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check(_lib.pic_set_allocator(hooks[0], hooks[1], None), "pic_set_allocator")
+    _torch_hooks = hooks
+
+
+def pic_set_allocator(alloc=None, free=None):
+    """Install ctypes-compatible alloc/free callbacks, or restore cudaMalloc (no args)."""
+    global _torch_hooks
+    if alloc is None:
+        _check(_lib.pic_set_allocator(_ALLOC_FN(), _FREE_FN(), None), "pic_set_allocator")
+        _torch_hooks = None
+        return
+    hooks = (_ALLOC_FN(alloc), _FREE_FN(free))
+    _check(_lib.pic_set_allocator(hooks[0], hooks[1], None), "pic_set_allocator")
+    _torch_hooks = hooks
+
+
+# ---- handles -------------------------------------------------------------------------
+class Mesh:
+    def __init__(self, ptr, precision):
+        self.ptr = ptr
+        self.precision = precision
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            _lib.pic_mesh_destroy(self.ptr)
+            self.ptr = None
+
+
+class Sim:
+    def __init__(self, ptr, mesh):
+        self.ptr = ptr
+        self.mesh = mesh          # the mesh must outlive the simulation
+        _live_sims.add(self)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            _lib.pic_sim_destroy(self.ptr)
+            self.ptr = None
+
+
+_live_sims = weakref.WeakSet()
+
+
+@atexit.register
+def _destroy_live_sims():
+    # free device memory while the allocator callbacks (torch) are still alive
+    for s in list(_live_sims):
+        if s.ptr:
+            _lib.pic_sim_destroy(s.ptr)
+            s.ptr = None
+
+
+def pic_mesh_create(nodes_zr, tris, bedge_nodes, bedge_tag, eps0=1.0, mu0=1.0, c=None,
+                    precision=PIC_FP32, walk_cap=0):
+    nodes_zr = _arr(nodes_zr, np.float64)
+    tris = _arr(tris, np.int32)
+    bedge_nodes = _arr(bedge_nodes, np.int32)
+    bedge_tag = _arr(bedge_tag, np.int32)
+    if c is None:
+        c = 1.0 / np.sqrt(eps0 * mu0)
+    u = pic_units(eps0, mu0, c, precision, walk_cap)
+    out = ctypes.c_void_p()
+    _check(_lib.pic_mesh_create(_ptr(nodes_zr), len(nodes_zr), _ptr(tris), len(tris),
+                                _ptr(bedge_nodes), _ptr(bedge_tag), len(bedge_tag),
+                                ctypes.byref(u), ctypes.byref(out)), "pic_mesh_create")
+    return Mesh(out, precision)
+
+
+def pic_mesh_info(mesh):
+    v = [ctypes.c_int64() for _ in range(5)]
+    _check(_lib.pic_mesh_info(mesh.ptr, *[ctypes.byref(x) for x in v]), "pic_mesh_info")
+    return dict(zip(["n_nodes", "n_edges", "n_tris", "n_free_edges", "spai_nnz"],
+                    [x.value for x in v]))
+
+
+def pic_mesh_edges(mesh):
+    n = pic_mesh_info(mesh)["n_edges"]
+    out = np.zeros((n, 2), np.int32)
+    _check(_lib.pic_mesh_edges(mesh.ptr, _ptr(out)), "pic_mesh_edges")
+    return out
+
+
+def pic_spai_build(mesh, pattern_level=2, drop_tol=1e-4):
+    dt = ctypes.c_double()
+    _check(_lib.pic_spai_build(mesh.ptr, pattern_level, drop_tol, ctypes.byref(dt)),
+           "pic_spai_build")
+    return dt.value
+
+
+def pic_spai_get(mesh):
+    info = pic_mesh_info(mesh)
+    nf, nnz = info["n_free_edges"], info["spai_nnz"]
+    fe = np.zeros(nf, np.int32)
+    ip = np.zeros(nf + 1, np.int64)
+    ix = np.zeros(nnz, np.int32)
+    vv = np.zeros(nnz, np.float64)
+    _check(_lib.pic_spai_get(mesh.ptr, _ptr(fe), _ptr(ip), _ptr(ix), _ptr(vv)), "pic_spai_get")
+    return fe, ip, ix, vv
+
+
+def pic_sim_create(mesh, dt, bz_guide=0.0, max_particles=0, torch_memory=True):
+    if torch_memory and _torch_hooks is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                use_torch_allocator()
+        except ImportError:
+            pass
+    out = ctypes.c_void_p()
+    _check(_lib.pic_sim_create(mesh.ptr, dt, bz_guide, int(max_particles), ctypes.byref(out)),
+           "pic_sim_create")
+    return Sim(out, mesh)
+
+
+def pic_sim_set_sort_interval(sim, interval):
+    _check(_lib.pic_sim_set_sort_interval(sim.ptr, interval), "pic_sim_set_sort_interval")
+
+
+def pic_fields_set(sim, E=None, B=None, stream=None):
+    E = None if E is None else _arr(E, np.float64)
+    B = None if B is None else _arr(B, np.float64)
+    _check(_lib.pic_fields_set(sim.ptr, _ptr(E), _ptr(B), _stream(stream)), "pic_fields_set")
+
+
+def pic_particles_inject(sim, z, rho, u_rho, u_phi, u_z, q, m, weight, stream=None):
+    z, rho, u_rho, u_phi, u_z = (_arr(x, np.float64) for x in (z, rho, u_rho, u_phi, u_z))
+    n = len(z)
+    assert all(len(x) == n for x in (rho, u_rho, u_phi, u_z))
+    _check(_lib.pic_particles_inject(sim.ptr, n, _ptr(z), _ptr(rho), _ptr(u_rho), _ptr(u_phi),
+                                     _ptr(u_z), q, m, weight, _stream(stream)),
+           "pic_particles_inject")
+
+
+def pic_step(sim, n_steps=1, stream=None):
+    _check(_lib.pic_step(sim.ptr, int(n_steps), _stream(stream)), "pic_step")
+
+
+def pic_diagnostics(sim, fields=False, stream=None):
+    d = pic_diag()
+    info = pic_mesh_info(sim.mesh)
+    E = B = J = None
+    if fields:
+        E = np.zeros(info["n_edges"])
+        B = np.zeros(info["n_tris"])
+        J = np.zeros(info["n_edges"])
+    _check(_lib.pic_diagnostics(sim.ptr, ctypes.byref(d), _ptr(E), _ptr(B), _ptr(J),
+                                _stream(stream)), "pic_diagnostics")
+    out = {k: getattr(d, k) for k, _ in pic_diag._fields_}
+    if fields:
+        out.update(E=E, B=B, J=J)
+    return out
+
+
+def pic_charges_get(sim, stream=None):
+    n0 = pic_mesh_info(sim.mesh)["n_nodes"]
+    Q, Qp, Qa = np.zeros(n0), np.zeros(n0), np.zeros(n0)
+    _check(_lib.pic_charges_get(sim.ptr, _ptr(Q), _ptr(Qp), _ptr(Qa), _stream(stream)),
+           "pic_charges_get")
+    return Q, Qp, Qa
+
+
+def pic_particles_count(sim, stream=None):
+    n = ctypes.c_int64()
+    _check(_lib.pic_particles_count(sim.ptr, ctypes.byref(n), _stream(stream)),
+           "pic_particles_count")
+    return n.value
+
+
+def pic_particles_get(sim, stream=None):
+    n = pic_particles_count(sim, stream)
+    pid = np.zeros(n, np.int64)
+    tri = np.zeros(n, np.int32)
+    lam = np.zeros((n, 3))
+    u = np.zeros((n, 3))
+    _check(_lib.pic_particles_get(sim.ptr, n, _ptr(pid), _ptr(tri), _ptr(lam), _ptr(u),
+                                  _stream(stream)), "pic_particles_get")
+    return dict(pid=pid, tri=tri, lam=lam, u=u)
+
+
+def pic_particles_raw_bytes(sim):
+    b = ctypes.c_int64()
+    _check(_lib.pic_particles_raw_bytes(sim.ptr, ctypes.byref(b)), "pic_particles_raw_bytes")
+    return b.value
+
+
+def pic_particles_raw_get(sim, host_ptr, n_slots, stream=None):
+    """host_ptr: address (int) of a page-locked buffer of n_slots * raw_bytes bytes."""
+    _check(_lib.pic_particles_raw_get(sim.ptr, ctypes.c_void_p(host_ptr), int(n_slots),
+                                      _stream(stream)), "pic_particles_raw_get")
+
+
+def pic_particles_raw_set(sim, host_ptr, n_slots, stream=None):
+    _check(_lib.pic_particles_raw_set(sim.ptr, ctypes.c_void_p(host_ptr), int(n_slots),
+                                      _stream(stream)), "pic_particles_raw_set")
+
+
+def pic_kernel_timing(sim, enable=True, stream=None):
+    """Returns (milliseconds, launches) of the particle kernel since the last call and
+    turns the per-launch CUDA-event timing on or off."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(_lib.pic_kernel_timing(sim.ptr, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(n),
+                                  _stream(stream)), "pic_kernel_timing")
+    return ms.value, n.value
+
+
+def pic_sim_destroy(sim):
+    if sim.ptr:
+        _lib.pic_sim_destroy(sim.ptr)
+        sim.ptr = None
+
+
+def pic_mesh_destroy(mesh):
+    if mesh.ptr:
+        _lib.pic_mesh_destroy(mesh.ptr)
+        mesh.ptr = None

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle on the same
+seeded inputs.  FP64 build: 1e-12 relative per step.  FP32 build (fixed-point positions
+and currents): 1e-5 relative per step, and the discrete continuity equation exact in
+integers."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import OracleSim
+from oracle.operators import Mesh
+from oracle import particles as OP
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import pic as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def cavity_oracle():
+    nodes, tris, be, bt = W.cavity_mesh()          # 0.5 x 1 cavity, ~2000 triangles
+    return (nodes, tris, be, bt), OracleSim(nodes, tris, be, bt)
+
+
+def _copy(o):
+    s = OracleSim.__new__(OracleSim)
+    s.__dict__.update(o.__dict__)
+    return s
+
+
+def _setup(pic, mesh_arrays, oracle, prec, n, seed, dt_frac=0.5, bz=0.3, sigma_u=0.3,
+           e_scale=0.05, walk_cap=0, sort_interval=4, cap=None):
+    nodes, tris, be, bt = mesh_arrays
+    o = _copy(oracle)
+    m = o.mesh
+    dt = dt_frac * o.dt_max
+    o.create(dt, bz=bz)
+    E0 = W.random_edge_values(m.N1, e_scale, seed)
+    B0 = W.random_edge_values(m.N2, 1e-3, seed + 1)
+    o.set_fields(E0, B0)
+    z, r, ur, up, uz = W.uniform_in_mesh(nodes, tris, n, seed + 2, sigma_u=sigma_u)
+    o.inject(z, r, ur, up, uz, -1.0, 1.0, 1e-3)
+    mesh = pic.pic_mesh_create(nodes, tris, be, bt, precision=prec, walk_cap=walk_cap)
+    pic.pic_spai_build(mesh)
+    sim = pic.pic_sim_create(mesh, dt, bz, cap or 2 * n + 16)
+    pic.pic_sim_set_sort_interval(sim, sort_interval)
+    pic.pic_fields_set(sim, E0, B0)
+    pic.pic_particles_inject(sim, z, r, ur, up, uz, -1.0, 1.0, 1e-3)
+    if walk_cap:
+        o_cap = walk_cap
+    else:
+        o_cap = OP.WALK_CAP
+    return o, sim, mesh, o_cap
+
+
+def _gpu_particles(pic, sim, n):
+    p = pic.pic_particles_get(sim)
+    tri = -np.ones(n, np.int64)
+    lam = np.zeros((n, 3))
+    u = np.zeros((n, 3))
+    live = p["tri"] >= 0
+    tri[p["pid"][live]] = p["tri"][live]
+    lam[p["pid"][live]] = p["lam"][live]
+    u[p["pid"][live]] = p["u"][live]
+    return tri, lam, u
+
+
+def _oracle_step(o, n_steps, cap):
+    for _ in range(n_steps):
+        B_half = o.field_b_half()
+        m = o.mesh
+        Bavg = 0.5 * (B_half + o.B)
+        o.J = np.zeros(m.N1)
+        Qn = np.zeros(m.N0)
+        o.Qabs = np.zeros(m.N0)
+        o.counters += OP.push(o.pm, o.E, Bavg, o.bz, o.dt, o.qm, o.c, o.q_src, o.tri, o.lam,
+                              o.u, o.J, Qn, o.Qabs, max_cross=cap)
+        o.field_e(B_half)
+        o.B = B_half
+        o.Q_prev, o.Q = o.Q, Qn
+
+
+def _positions(nodes, tris, tri, lam):
+    p = nodes[tris[np.maximum(tri, 0)]]
+    return np.einsum("nk,nkd->nd", lam, p)
+
+
+@pytest.mark.parametrize("steps", [1, 5])
+def test_fp64_matches_oracle(pic, cavity_oracle, steps):
+    """FP64 build: particle state, fields and scatter within 1e-12 of the oracle."""
+    arrays, oracle = cavity_oracle
+    n = 10_000
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP64, n, seed=10)
+    pic.pic_step(sim, steps)
+    _oracle_step(o, steps, cap)
+    d = pic.pic_diagnostics(sim, fields=True)
+    tri, lam, u = _gpu_particles(pic, sim, n)
+    assert np.array_equal(tri, o.tri)
+    live = o.tri >= 0
+    tol = 1e-12 * steps
+    assert np.abs(lam[live] - o.lam[live]).max() < tol
+    assert np.abs(u[live] - o.u[live]).max() < tol * np.abs(o.u).max()
+    assert np.abs(d["E"] - o.E).max() < tol * np.abs(o.E).max()
+    assert np.abs(d["B"] - o.B).max() < tol * np.abs(o.B).max()
+    assert np.abs(d["J"] - o.J).max() < tol * np.abs(o.J).max()
+    Q, Qp, Qa = pic.pic_charges_get(sim)
+    assert np.abs(Q - o.Q).max() < tol * np.abs(o.Q).max()
+    assert np.abs(Qa - o.Qabs).max() < tol * max(np.abs(o.Q).max(), 1e-30)
+    assert d["n_absorbed"] == o.counters[0] and d["n_crossings"] == o.counters[2]
+    assert d["dce_max"] < 1e-12 and d["dgl_drift"] < 1e-12
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+def test_fp32_matches_oracle(pic, cavity_oracle, steps):
+    """FP32 build: 1e-5 relative per step; triangle ids equal except within 1e-5 of an edge."""
+    arrays, oracle = cavity_oracle
+    nodes, tris = arrays[0], arrays[1]
+    n = 10_000
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, n, seed=20)
+    pic.pic_step(sim, steps)
+    _oracle_step(o, steps, cap)
+    d = pic.pic_diagnostics(sim, fields=True)
+    tri, lam, u = _gpu_particles(pic, sim, n)
+    tol = 1e-5
+    live = o.tri >= 0
+    assert np.array_equal(tri >= 0, live)
+    h = math.sqrt(2 * o.mesh.area.mean())
+    xg = _positions(nodes, o.mesh.tris, tri, lam)
+    xo = _positions(nodes, o.mesh.tris, o.tri, o.lam)
+    assert np.abs(xg[live] - xo[live]).max() < tol * h
+    interior = live & (o.lam.min(1) > 1e-5)
+    assert np.array_equal(tri[interior], o.tri[interior])
+    assert np.abs(u[live] - o.u[live]).max() < tol * np.abs(o.u).max()
+    assert np.abs(d["E"] - o.E).max() < tol * np.abs(o.E).max()
+    assert np.abs(d["B"] - o.B).max() < tol * np.abs(o.B).max()
+    assert np.abs(d["J"] - o.J).max() < tol * np.abs(o.J).max()
+    # charge conservation is exact in the fixed-point build
+    assert d["dce_nonzero"] == 0 and d["dce_max"] == 0.0
+    Q, Qp, Qa = pic.pic_charges_get(sim)
+    assert np.abs(Q - o.Q).max() < tol * np.abs(o.Q).max()
+
+
+def test_fp32_dce_exact_over_many_steps(pic, cavity_oracle):
+    """50 steps with re-sorting every 3 steps: the fixed-point DCE residual is exactly zero
+    at every step, the DGL residual stays constant, and total charge is conserved."""
+    arrays, oracle = cavity_oracle
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, 20_000, seed=30,
+                               sigma_u=0.8, sort_interval=3)
+    q0 = pic.pic_charges_get(sim)[0].sum()
+    qabs = 0.0
+    for k in range(50):
+        pic.pic_step(sim, 1)
+        d = pic.pic_diagnostics(sim)
+        assert d["dce_nonzero"] == 0, k
+        Q, Qp, Qa = pic.pic_charges_get(sim)
+        qabs += Qa.sum()
+        assert abs(Q.sum() + qabs - q0) <= 1e-12 * abs(q0)
+    assert d["dgl_drift"] < 1e-5
+    assert d["n_absorbed"] > 0 and d["n_crossings"] > 0
+
+
+def test_walk_cap_and_empty(pic, cavity_oracle):
+    """walk_cap = 1 removes a particle at its second crossing, as in the oracle; a
+    simulation without particles steps its fields like the oracle."""
+    arrays, oracle = cavity_oracle
+    n = 5000
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP64, n, seed=40, sigma_u=3.0,
+                               walk_cap=1)
+    pic.pic_step(sim, 2)
+    _oracle_step(o, 2, cap)
+    d = pic.pic_diagnostics(sim)
+    assert d["walk_overflows"] == o.counters[1] and d["n_absorbed"] == o.counters[0]
+    tri, lam, u = _gpu_particles(pic, sim, n)
+    assert np.array_equal(tri, o.tri)
+
+    o2 = _copy(oracle)
+    o2.create(0.5 * o2.dt_max)
+    m = o2.mesh
+    E0 = W.tm0np_edge_dofs(m.nodes, m.edge_nodes, 0.5, 1.0, 1, 1)
+    o2.set_fields(E0, np.zeros(m.N2))
+    mesh2 = pic.pic_mesh_create(*arrays, precision=pic.PIC_FP64)
+    pic.pic_spai_build(mesh2)
+    sim2 = pic.pic_sim_create(mesh2, o2.dt, 0.0, 0)
+    pic.pic_fields_set(sim2, E0, np.zeros(m.N2))
+    pic.pic_step(sim2, 20)
+    o2.step(20)
+    d2 = pic.pic_diagnostics(sim2, fields=True)
+    assert np.abs(d2["E"] - o2.E).max() < 1e-12 * np.abs(o2.E).max()
+    assert d2["n_particles"] == 0
+
+
+def test_rest_particles_are_bit_exact(pic, cavity_oracle):
+    """Particles at rest in zero fields keep their fixed-point coordinates bit for bit and
+    deposit no current."""
+    arrays, oracle = cavity_oracle
+    nodes, tris, be, bt = arrays
+    mesh = pic.pic_mesh_create(nodes, tris, be, bt, precision=pic.PIC_FP32)
+    dt = 0.5 * pic.pic_spai_build(mesh)
+    sim = pic.pic_sim_create(mesh, dt, 0.0, 1000)
+    z, r, *_ = W.uniform_in_mesh(nodes, tris, 500, 7)
+    zero = np.zeros(500)
+    pic.pic_particles_inject(sim, z, r, zero, zero, zero, -1.0, 1.0, 1e-3)
+    p0 = pic.pic_particles_get(sim)
+    pic.pic_step(sim, 3)
+    p1 = pic.pic_particles_get(sim)
+    o0, o1 = np.argsort(p0["pid"]), np.argsort(p1["pid"])
+    assert np.array_equal(p0["tri"][o0], p1["tri"][o1])
+    assert np.array_equal(p0["lam"][o0], p1["lam"][o1])
+    d = pic.pic_diagnostics(sim, fields=True)
+    assert np.all(d["J"] == 0) and np.all(d["E"] == 0)
+
+
+def test_resort_orders_by_triangle(pic, cavity_oracle):
+    arrays, oracle = cavity_oracle
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, 30_000, seed=50, sigma_u=1.0,
+                               sort_interval=2)
+    pic.pic_step(sim, 4)
+    p = pic.pic_particles_get(sim)
+    assert np.all(np.diff(p["tri"]) >= 0) and p["tri"][0] >= 0
+    d = pic.pic_diagnostics(sim)
+    assert len(p["pid"]) == d["n_particles"]
+    assert len(np.unique(p["pid"])) == len(p["pid"])
+
+
+def test_raw_roundtrip(pic, cavity_oracle):
+    """Host round trip of the raw state leaves the simulation unchanged."""
+    import torch
+    arrays, oracle = cavity_oracle
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, 4000, seed=60)
+    n = pic.pic_particles_count(sim)
+    b = pic.pic_particles_raw_bytes(sim)
+    assert b == 24
+    buf = torch.empty(n * b, dtype=torch.uint8, pin_memory=True)
+    before = pic.pic_particles_get(sim)
+    pic.pic_particles_raw_get(sim, buf.data_ptr(), n)
+    torch.cuda.synchronize()
+    pic.pic_particles_raw_set(sim, buf.data_ptr(), n)
+    torch.cuda.synchronize()
+    after = pic.pic_particles_get(sim)
+    for k in ("tri", "lam", "u"):
+        assert np.array_equal(before[k], after[k])

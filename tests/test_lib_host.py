@@ -1,0 +1,91 @@
+"""The C-ABI library on the CPU: it loads, exports every function include/pic.h declares,
+rejects bad meshes, and its host-side setup (edge numbering, SPAI, stable step) matches
+the oracle.  No GPU needed: these calls do not touch the device."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.operators import Mesh, hodge_eps, hodge_mu_inv, spai, dt_stable
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pic():
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import pic as p
+    return p
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(pic):
+    names = _declared()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", pic.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert set(pic.EXPORTED) <= set(names)
+
+
+def test_bad_meshes_are_rejected(pic):
+    nodes, tris, be, bt = W.two_triangle_mesh()
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mesh_create(nodes, np.array([[0, 1, 1], [0, 2, 3]]), be, bt)
+    assert e.value.status == pic.PIC_ERR_MESH
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mesh_create(nodes, tris, be[:3], bt[:3])          # a boundary edge untagged
+    assert e.value.status == pic.PIC_ERR_MESH
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mesh_create(nodes, np.array([[0, 1, 9], [0, 2, 3]]), be, bt)
+    assert e.value.status == pic.PIC_ERR_ARG
+    bad = nodes.copy()
+    bad[0, 1] = -0.1
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mesh_create(bad, tris, be, bt)
+    assert e.value.status == pic.PIC_ERR_ARG
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mesh_create(nodes, tris, np.vstack([be, [[0, 2]]]), np.append(bt, 1))
+    assert e.value.status == pic.PIC_ERR_MESH                     # interior edge listed
+    m = pic.pic_mesh_create(nodes, tris, be, bt)
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_sim_create(m, 0.01)                               # no SPAI yet
+    assert e.value.status == pic.PIC_ERR_STATE
+    assert "pic_sim_create" in pic.pic_last_error()
+
+
+@pytest.mark.parametrize("which", ["cavity", "bwo_small", "four"])
+def test_host_setup_matches_oracle(pic, which):
+    mk = {"cavity": lambda: W.cavity_mesh(n_tri=600, seed=3),
+          "bwo_small": lambda: W.bwo_small_mesh(n_tri=3000, seed=4),
+          "four": W.four_triangle_mesh}[which]
+    nodes, tris, be, bt = mk()
+    eps0, mu0 = (8.8541878128e-12, 1.25663706212e-6) if which == "bwo_small" else (1.0, 1.0)
+    om = Mesh(nodes, tris, be, bt)
+    m = pic.pic_mesh_create(nodes, tris, be, bt, eps0=eps0, mu0=mu0)
+    info = pic.pic_mesh_info(m)
+    assert (info["n_nodes"], info["n_edges"], info["n_tris"]) == (om.N0, om.N1, om.N2)
+    assert np.array_equal(pic.pic_mesh_edges(m), om.edge_nodes)
+    assert info["n_free_edges"] == len(om.free)
+    level = 2 if which != "four" else 6
+    dt = pic.pic_spai_build(m, level, 1e-4 if which != "four" else 0.0)
+    fe, ip, ix, vv = pic.pic_spai_get(m)
+    assert np.array_equal(fe, om.free)
+    A = hodge_eps(om, eps0)
+    M = spai(om, A, level, 1e-4 if which != "four" else 0.0).tocsr()
+    M.sort_indices()
+    assert np.array_equal(ip, M.indptr) and np.array_equal(ix, M.indices)
+    assert np.allclose(vv, M.data, rtol=1e-9, atol=1e-12 * np.abs(M.data).max())
+    dt_o, _ = dt_stable(om, M, hodge_mu_inv(om, mu0))
+    assert abs(dt - dt_o) <= 1e-9 * dt_o
