@@ -69,6 +69,20 @@ __device__ __forceinline__ void quantize(const float in[3], Bary<PF32> &out) {
     for (int k = 0; k < 3; k++) out.f[k] = (float)out.q[k] * (float)LAM_INV;
 }
 
+// A point on local edge kx: coordinate kx is exactly 0 and the other two are integers
+// that sum to 2^22 (the neighbour inherits them unchanged).
+__device__ __forceinline__ void quantize_on_edge(int kx, float ci, float cj, Bary<PF32> &out) {
+    const int ii = (kx + 1) % 3, jj = (kx + 2) % 3;
+    ci = fmaxf(ci, 0.f);
+    cj = fmaxf(cj, 0.f);
+    int32_t qi = __float2int_rn(ci / (ci + cj) * (float)LAM_ONE);
+    qi = min(max(qi, 0), LAM_ONE);
+    out.q[kx] = 0;
+    out.q[ii] = qi;
+    out.q[jj] = LAM_ONE - qi;
+    for (int k = 0; k < 3; k++) out.f[k] = (float)out.q[k] * (float)LAM_INV;
+}
+
 // segment current on the three edges of triangle `rec`: lam_a^s lam_b^e - lam_b^s lam_a^e
 // for each local edge with tail a and head b (Eq. current as the line integral of W1)
 __device__ __forceinline__ void segment_current(const int32_t flags, const Bary<PF32> &s,
@@ -217,11 +231,7 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<P> a) {
                 int ii = (kx + 1) % 3, jj = (kx + 2) % 3;
                 R ci = l.f[ii] + sx * dl[ii], cj = l.f[jj] + sx * dl[jj];
                 if constexpr (P::fixed) {
-                    float tmp[3];
-                    tmp[kx] = 0.f;
-                    tmp[ii] = ci;
-                    tmp[jj] = cj;
-                    quantize(tmp, e);
+                    quantize_on_edge(kx, ci, cj, e);
                 } else {
                     double sum = ci + cj;
                     e.f[kx] = 0.0;

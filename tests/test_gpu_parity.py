@@ -33,8 +33,14 @@ def cavity_oracle():
 
 
 def _copy(o):
+    """A fresh oracle state sharing only the read-only operators of a prepared one."""
     s = OracleSim.__new__(OracleSim)
-    s.__dict__.update(o.__dict__)
+    s.__dict__.update({k: (v.copy() if isinstance(v, np.ndarray) else v)
+                       for k, v in o.__dict__.items()})
+    m = s.mesh
+    s.Q, s.Q_prev, s.Qabs = np.zeros(m.N0), np.zeros(m.N0), np.zeros(m.N0)
+    s.J = np.zeros(m.N1)
+    s.counters = np.zeros(3, np.int64)
     return s
 
 
