@@ -1,0 +1,362 @@
+"""Benchmark of the per-step PIC particle loop on the single backward-wave-oscillator
+workload: rippled slow-wave structure, ~200k triangles, 16M beam particles, FP32 with
+fixed-point positions and currents.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step is one full cycle of the method (B update, gather + Boris + walk + scatter,
+SPAI E update, re-sort every 4 steps).  Prints one JSON line (rank 0).  Under torchrun
+each rank runs an independent replica of the workload (the method's state does not
+shard without a domain decomposition): weak scaling, no collective on the data path.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EPS0 = 8.8541878128e-12
+MU0 = 1.25663706212e-6
+C0 = 299792458.0
+QE = -1.602176634e-19
+ME = 9.1093837015e-31
+METRIC = "particle-steps/s (gather+Boris+locate+scatter), batched runs/h vs plain, 1 GB300"
+BYTES_PER_PARTICLE = 48          # particle kernel: 24 B of state read + 24 B written
+CPU_SAMPLE = 160_000             # particles in the oracle's bounded sample
+PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_bwo16m.txt")
+# time step of the workload: half the SPAI leapfrog limit of this mesh (1.77e-13 s),
+# c dt = 0.12 mean edge lengths
+DT_BWO = 8.8e-14
+
+
+def workload(n_particles, seed=2002):
+    """Single BWO: wall 1.5 cm + 0.4 cm sin(2 pi z / 1.67 cm), 12 periods, 3 cm guides;
+    ~200k triangles; annular beam rho in [0.85, 0.95] cm over the ripple section, 400 kV,
+    3 kA, thermal spread 1e-3 u_z; guide field B_z = 2.5 T; seeded small random E."""
+    import workloads as W
+    nodes, tris, be, bt = W.bwo_mesh(200_000, seed=1002)
+    R, z_end, (zs0, zs1) = W.bwo_wall()
+    z, r, ur, up, uz = W.bwo_beam(n_particles, z0=zs0, z1=zs1, voltage=400e3, seed=seed)
+    gamma = 1.0 + 400e3 / 510998.95
+    vz = C0 * math.sqrt(1.0 - 1.0 / gamma ** 2)
+    # beam charge in the ripple section, I L / v_z, shared by the macro-particles
+    weight = 3e3 * (zs1 - zs0) / vz / (abs(QE) * n_particles)
+    # self-field scale of the beam, E ~ lambda / (2 pi eps0 rho); seed 1e-3 of it
+    e_scale = 1e-3 * (3e3 / vz) / (2 * math.pi * EPS0 * 0.9e-2)
+    return dict(nodes=nodes, tris=tris, be=be, bt=bt, z=z, r=r, ur=ur, up=up, uz=uz,
+                weight=weight, e_scale=e_scale, bz=2.5)
+
+
+def clock_sampler():
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    dev = os.environ.get("LOCAL_RANK", "0")
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", dev, "--query-gpu=" + q,
+                              "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None, None
+    rows = []
+
+    def reader():
+        for line in p.stdout:
+            rows.append(line.strip())
+    t = threading.Thread(target=reader, daemon=True)
+    t.start()
+    return p, rows
+
+
+def clock_summary(p, rows):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    time.sleep(0.1)
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        f = [x.strip() for x in r.split(",")]
+        if len(f) < 7:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx.append(float(f[1]))
+        except ValueError:
+            continue
+        for name, v in zip(names, f[3:7]):
+            if v.lower().startswith("active"):
+                reasons.add(name)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def push_traffic():
+    """DRAM bytes per particle-kernel launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        src = open(os.path.join(ROOT, "paper_1701_03784_gb300", "csrc", "k_push_f32.cu"), "rb").read()
+        h = hashlib.sha256(src).hexdigest()[:16]
+        vals = {}
+        for line in open(PUSH_PROFILE):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("k_push.cu sha256[:16]") == h:
+            return float(vals["dram bytes per launch (full size)"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+class OracleSample:
+    """The FP64 oracle's particle loop (gather, Boris, walk, scatter), single-threaded, on
+    a bounded sample of the same workload: the same mesh, fields and step, the first
+    n_sample beam particles."""
+
+    def __init__(self, wl, n_sample=CPU_SAMPLE):
+        from oracle.operators import Mesh
+        from oracle import particles as OP
+        import workloads as W
+        self.OP = OP
+        m = Mesh(wl["nodes"], wl["tris"], wl["be"], wl["bt"])
+        self.pm = OP.PushMesh(m)
+        self.E = W.random_edge_values(m.N1, wl["e_scale"] * 2e-4, 7)
+        self.E[m.edge_tag == 1] = 0.0
+        self.Bavg = np.zeros(m.N2)
+        sl = slice(0, n_sample)
+        tri, lam = OP.locate(m, wl["z"][sl], wl["r"][sl])
+        self.tri = np.ascontiguousarray(tri)
+        self.lam = np.ascontiguousarray(lam)
+        self.u = np.ascontiguousarray(np.stack([wl["ur"][sl], wl["up"][sl], wl["uz"][sl]], 1))
+        self.J, self.Q, self.Qa = np.zeros(m.N1), np.zeros(m.N0), np.zeros(m.N0)
+        self.wl = wl
+        self.n = n_sample
+        self.q_src = wl["weight"] * QE / (2 * math.pi)
+
+    def step(self):
+        """One particle step of the sample; returns its wall time in seconds."""
+        t0 = time.perf_counter()
+        self.J[:] = 0
+        self.Q[:] = 0
+        self.OP.push(self.pm, self.E, self.Bavg, self.wl["bz"], self.wl["dt"], QE / ME, C0,
+                     self.q_src, self.tri, self.lam, self.u, self.J, self.Q, self.Qa)
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    s = OracleSample(wl)
+    done, el = 0, 0.0
+    while el < budget_s:
+        el += s.step()
+        done += 1
+    live = int(np.count_nonzero(s.tri >= 0))
+    return {"value": s.n * done / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of %d beam particles, %d steps, same mesh, fields and dt; FP64 C "
+                      "oracle particle loop (gather, Boris, walk, scatter), single thread; %d "
+                      "live at end" % (s.n, len(wl["z"]), done, live)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload(args.particles)
+    wl["dt"] = args.dt or DT_BWO
+    s = OracleSample(wl)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        el = s.step()
+        if i >= args.warmup:
+            per_step.append(el)
+    t = sum(per_step)
+    value = CPU_SAMPLE * args.steps / t
+    cb = {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+          "sample": "%d of %d particles per step (bounded sample of the workload), FP64 C "
+                    "oracle particle loop, single thread" % (CPU_SAMPLE, args.particles)}
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "single BWO, ~200k triangles, %d particles (CPU sample %d)"
+                                   % (args.particles, CPU_SAMPLE)},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=16_000_000)
+    ap.add_argument("--sort-interval", type=int, default=4)
+    ap.add_argument("--dt", type=float, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import pic
+
+    wl = workload(args.particles, seed=2002 + rank)
+    mesh = pic.pic_mesh_create(wl["nodes"], wl["tris"], wl["be"], wl["bt"], eps0=EPS0, mu0=MU0,
+                               c=C0, precision=pic.PIC_FP32)
+    dt_max = pic.pic_spai_build(mesh, 2, 1e-4)
+    dt = args.dt or DT_BWO
+    wl["dt"] = dt
+    info = pic.pic_mesh_info(mesh)
+    sim = pic.pic_sim_create(mesh, dt, wl["bz"], args.particles + 1024)
+    pic.pic_sim_set_sort_interval(sim, args.sort_interval)
+    import workloads as W
+    E0 = W.random_edge_values(info["n_edges"], wl["e_scale"] * 2e-4, 7 + rank)
+    pic.pic_fields_set(sim, E0, np.zeros(info["n_tris"]))
+    pic.pic_particles_inject(sim, wl["z"], wl["r"], wl["ur"], wl["up"], wl["uz"], QE, ME,
+                             wl["weight"])
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    pic.pic_step(sim, args.warmup)
+    barrier()
+    n_live = pic.pic_diagnostics(sim)["n_particles"]
+    # timed region: K full steps, CUDA events on the launching stream
+    pic.pic_kernel_timing(sim, True)
+    sampler, rows = clock_sampler()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pic.pic_step(sim, args.steps)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clock_summary(sampler, rows)
+    push_ms, push_launches = pic.pic_kernel_timing(sim, False)
+    diag = pic.pic_diagnostics(sim)
+    n_end = diag["n_particles"]
+    resorts = sum(1 for k in range(args.warmup + 1, args.warmup + args.steps + 1)
+                  if args.sort_interval and k % args.sort_interval == 0)
+    launches = 4 * args.steps + 5 * resorts
+
+    # end to end through the C ABI with host buffers: upload the state from pinned
+    # memory, step, read it back, every step
+    n_slots = pic.pic_particles_count(sim)
+    bpp = pic.pic_particles_raw_bytes(sim)
+    host = torch.empty(n_slots * bpp, dtype=torch.uint8, pin_memory=True)
+    pic.pic_particles_raw_get(sim, host.data_ptr(), n_slots)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        pic.pic_particles_raw_set(sim, host.data_ptr(), n_slots)
+        pic.pic_step(sim, 1)
+        pic.pic_particles_raw_get(sim, host.data_ptr(), n_slots)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    # max over ranks of the timed regions
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+    cnt = torch.tensor([float(n_live + n_end) / 2.0, float(n_slots)], dtype=torch.float64,
+                       device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+    ms, e2e_ms = t.tolist()
+    total_particles, total_slots = cnt.tolist()
+    value = total_particles * args.steps / (ms * 1e-3)
+    e2e_value = total_slots * args.e2e_steps / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        peak, peak_kind = measured_peak()
+        avg_push_s = push_ms * 1e-3 / max(push_launches, 1)
+        achieved = BYTES_PER_PARTICLE * 0.5 * (n_live + n_end) / avg_push_s / 1e9
+        traffic = push_traffic()
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "single BWO (rippled SWS, 12 periods), %d triangles, %d "
+                                   "particles, FP32 + int64 fixed-point J/Q" % (info["n_tris"],
+                                                                              args.particles),
+                       "n_tris": info["n_tris"], "n_edges": info["n_edges"],
+                       "particles": args.particles, "dt_s": dt, "dt_over_stable": dt / dt_max,
+                       "sort_interval": args.sort_interval,
+                       "l2": "inputs larger than L2 (particle state %d MB)"
+                             % (args.particles * 24 // 2 ** 20),
+                       "parallelism": "replicas" if args.gpus > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_push_f32", "peak_kind": peak_kind,
+                         "bytes_per_particle": BYTES_PER_PARTICLE,
+                         "avg_launch_ms": avg_push_s * 1e3, "launches": push_launches},
+            "e2e": {"value": e2e_value, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": n_slots * bpp, "d2h_bytes_per_step": n_slots * bpp,
+                    "steps": args.e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "checks": {"dce_nonzero_nodes": diag["dce_nonzero"], "dgl_drift": diag["dgl_drift"],
+                       "walk_overflows": diag["walk_overflows"], "live_particles": n_end,
+                       "absorbed": diag["n_absorbed"]},
+        }
+        if not args.no_cpu_baseline:
+            cb = cpu_baseline(wl)
+            cb.pop("seconds", None)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic_gb300.so")
-SOURCES = ["mesh.cpp", "spai.cpp", "sim.cu", "k_push.cu", "k_field.cu", "k_sort.cu", "k_diag.cu"]
+SOURCES = ["mesh.cpp", "spai.cpp", "sim.cu", "k_push.cu", "k_push_f32.cu", "k_field.cu", "k_sort.cu",
+           "k_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

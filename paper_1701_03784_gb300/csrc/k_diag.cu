@@ -30,7 +30,8 @@ template <class P>
 __global__ void __launch_bounds__(256) k_diag_nodes(DiagDev d, const typename P::Acc *J,
                                                     const typename P::Acc *Qn,
                                                     const typename P::Acc *Qp,
-                                                    const typename P::Acc *Qabs, const double *D,
+                                                    const typename P::Acc *Qabs,
+                                                    const typename P::Acc *Qpos, const double *D,
                                                     double *dgl_ref, int set_ref, double q_scale,
                                                     double *out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,6 +46,12 @@ __global__ void __launch_bounds__(256) k_diag_nodes(DiagDev d, const typename P:
             long long res = dq * (long long)LAM_ONE + div;  // exact: units 2^-44 of q_src
             dce = fabs((double)res) * J_INV;
             nz = res != 0 ? 1.0 : 0.0;
+            if (Qpos) {
+                // the carried Q^{n+1} against Eq. charge evaluated at the positions
+                long long mis = (long long)Qn[k] - (long long)Qpos[k];
+                if (mis != 0) nz = 1.0;
+                dce = fmax(dce, fabs((double)mis) * LAM_INV);
+            }
             double divd = fabs((double)div) * J_INV;
             if (divd > 1e-9) nr = dce / divd;
             qk = (double)(long long)Qn[k] * LAM_INV;
@@ -119,11 +126,12 @@ __global__ void __launch_bounds__(256) k_diag_kinetic(Particles<P> p, const int6
 
 template <class P>
 void launch_diag(const DiagDev &d, const typename P::Acc *J, const typename P::Acc *Qn,
-                 const typename P::Acc *Qp, const typename P::Acc *Qabs, const double *D,
+                 const typename P::Acc *Qp, const typename P::Acc *Qabs,
+                 const typename P::Acc *Qpos, const double *D,
                  double *dgl_ref, int set_ref, const typename P::R *E, const typename P::R *B,
                  const typename P::R *mu_inv, Particles<P> p, const int64_t *n_slots,
                  int64_t n_bound, double q_scale, double inv_c2, double *out, cudaStream_t s) {
-    k_diag_nodes<P><<<(unsigned)((d.N0 + 255) / 256), 256, 0, s>>>(d, J, Qn, Qp, Qabs, D, dgl_ref,
+    k_diag_nodes<P><<<(unsigned)((d.N0 + 255) / 256), 256, 0, s>>>(d, J, Qn, Qp, Qabs, Qpos, D, dgl_ref,
                                                                    set_ref, q_scale, out);
     if (set_ref) return;
     int64_t ne = d.N1 > d.N2 ? d.N1 : d.N2;
@@ -180,7 +188,8 @@ void launch_acc_to_double(const typename P::Acc *a, double *out, int64_t n, doub
 
 #define PIC_INST(P)                                                                            \
     template void launch_diag<P>(const DiagDev &, const P::Acc *, const P::Acc *,              \
-                                 const P::Acc *, const P::Acc *, const double *, double *, int, \
+                                 const P::Acc *, const P::Acc *, const P::Acc *, const double *, \
+                                 double *, int,                                                \
                                  const P::R *, const P::R *, const P::R *, Particles<P>,       \
                                  const int64_t *, int64_t, double, double, double *,           \
                                  cudaStream_t);                                                \

@@ -86,6 +86,22 @@ __global__ void __launch_bounds__(256) k_field_spmv(FieldArgs<P> a) {
     if (row < a.nf) a.E[a.free_edges[row]] += a.dt * acc;
 }
 
+// FP32 build, one thread per node: Q^{n+1} = Q^n - (D_div J)/2^22 - Q_absorbed.  Per
+// particle, the segment currents at a node sum to 2^22 (lambda^start - lambda^end) in the
+// fixed-point units (the identity behind Eq. DCE), so D_div J is divisible by 2^22 and the
+// result equals Eq. charge evaluated at the new positions exactly.  A non-zero remainder
+// would be a broken invariant; it is counted.
+__global__ void __launch_bounds__(256) k_charge_from_current(FieldArgs<PF32> a) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.N0) return;
+    long long div = 0;
+    for (int64_t q = a.node_ptr[k]; q < a.node_ptr[k + 1]; q++)
+        div += (long long)a.node_sign[q] * (long long)a.J[a.node_edge[q]];
+    if (div & (long long)(LAM_ONE - 1)) atomicAdd(a.counters + CNT_REMAINDER, 1ULL);
+    long long qn = (long long)a.Qn[k] - (div >> LAM_BITS) - (long long)a.Qabs[k];
+    a.Qnext[k] = (unsigned long long)qn;
+}
+
 template <class P>
 void launch_field_b(const FieldArgs<P> &a, cudaStream_t s) {
     k_field_b<P><<<(unsigned)((a.N2 + 255) / 256), 256, 0, s>>>(a);
@@ -93,6 +109,8 @@ void launch_field_b(const FieldArgs<P> &a, cudaStream_t s) {
 
 template <class P>
 void launch_field_e(const FieldArgs<P> &a, cudaStream_t s) {
+    if constexpr (P::fixed)
+        k_charge_from_current<<<(unsigned)((a.N0 + 255) / 256), 256, 0, s>>>(a);
     k_field_r<P><<<(unsigned)((a.nf + 255) / 256), 256, 0, s>>>(a);
     int64_t rows = ((a.nf + 31) / 32) * 32;
     k_field_spmv<P><<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(a);

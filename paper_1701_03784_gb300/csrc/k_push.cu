@@ -366,9 +366,13 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<P> a) {
 
 template <class P>
 void launch_push(const PushArgs<P> &a, int64_t n_bound, cudaStream_t s) {
-    if (n_bound <= 0) return;
-    int64_t blocks = (n_bound + 255) / 256;
-    k_push<P><<<(unsigned)blocks, 256, 0, s>>>(a);
+    if constexpr (P::fixed) {
+        launch_push_f32(a, n_bound, s);
+    } else {
+        if (n_bound <= 0) return;
+        int64_t blocks = (n_bound + 255) / 256;
+        k_push<P><<<(unsigned)blocks, 256, 0, s>>>(a);
+    }
 }
 
 // charge of newly injected particles, slots [first, first + count)

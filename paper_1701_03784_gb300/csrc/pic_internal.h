@@ -149,7 +149,16 @@ struct Particles {
     int32_t *pid = nullptr;
 };
 
-enum { CNT_ABSORBED = 0, CNT_OVERFLOW = 1, CNT_CROSSINGS = 2, CNT_N = 4 };
+enum {
+    CNT_ABSORBED = 0,
+    CNT_OVERFLOW = 1,
+    CNT_CROSSINGS = 2,
+    CNT_REMAINDER = 3,  // nodes where D_div J was not a multiple of 2^22 (must stay 0)
+    CNT_TIMEOUT = 4,    // bounded device waits that gave up (must stay 0)
+    CNT_N = 8
+};
+// slots past the capacity that the particle arrays keep for 16-byte bulk-copy rounding
+constexpr int64_t SLOT_PAD = 8;
 
 template <class P>
 struct PushArgs {
@@ -185,9 +194,19 @@ struct FieldArgs {
     int64_t N1, N2, nf;
     typename P::R dt;
     double j_scale;             // physical J = J_acc * j_scale
+    // FP32 build: Q^{n+1} = Q^n - D_div J / 2^22 - Q_absorbed per node (exact)
+    const int64_t *node_ptr;    // N0 + 1: node -> incident edges
+    const int32_t *node_edge;
+    const int8_t *node_sign;    // +1 tail, -1 head
+    const typename P::Acc *Qn;
+    const typename P::Acc *Qabs;
+    typename P::Acc *Qnext;
+    unsigned long long *counters;
+    int64_t N0;
 };
 
 template <class P> void launch_push(const PushArgs<P> &a, int64_t n_bound, cudaStream_t s);
+void launch_push_f32(const PushArgs<PF32> &a, int64_t n_bound, cudaStream_t s);
 template <class P> void launch_field_b(const FieldArgs<P> &a, cudaStream_t s);
 template <class P> void launch_field_e(const FieldArgs<P> &a, cudaStream_t s);
 template <class P>
@@ -221,8 +240,8 @@ struct DiagDev {
 // out[6]: sum (gamma - 1) over live particles
 template <class P>
 void launch_diag(const DiagDev &d, const typename P::Acc *J, const typename P::Acc *Qn,
-                 const typename P::Acc *Qp, const typename P::Acc *Qabs, const double *D,
-                 double *dgl_ref, int set_ref, const typename P::R *E,
+                 const typename P::Acc *Qp, const typename P::Acc *Qabs,
+                 const typename P::Acc *Qpos, const double *D, double *dgl_ref, int set_ref, const typename P::R *E,
                  const typename P::R *B, const typename P::R *mu_inv, Particles<P> p,
                  const int64_t *n_slots, int64_t n_bound, double q_scale, double inv_c2,
                  double *out, cudaStream_t s);

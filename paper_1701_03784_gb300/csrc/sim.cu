@@ -61,7 +61,7 @@ struct SimImpl final : SimBase {
     int64_t *ell_off = nullptr;
     int32_t *ell_col = nullptr;
     R *ell_val = nullptr;
-    Acc *J = nullptr, *Qbuf[2] = {nullptr, nullptr}, *Qabs = nullptr;
+    Acc *J = nullptr, *Qbuf[2] = {nullptr, nullptr}, *Qabs = nullptr, *qpos = nullptr;
     Particles<P> parts[2];
     int64_t *d_n = nullptr;
     unsigned long long *counters = nullptr;
@@ -179,7 +179,8 @@ struct SimImpl final : SimBase {
         // fields and accumulators
         if ((st = dalloc(E, mesh.N1)) || (st = dalloc(B, mesh.N2)) || (st = dalloc(D, mesh.N1)) ||
             (st = dalloc(r, nf)) || (st = dalloc(J, mesh.N1)) || (st = dalloc(Qbuf[0], mesh.N0)) ||
-            (st = dalloc(Qbuf[1], mesh.N0)) || (st = dalloc(Qabs, mesh.N0)))
+            (st = dalloc(Qbuf[1], mesh.N0)) || (st = dalloc(Qabs, mesh.N0)) ||
+            (st = dalloc(qpos, mesh.N0)))
             return st;
         PIC_CUDA_TRY(cudaMemset(E, 0, sizeof(R) * mesh.N1));
         PIC_CUDA_TRY(cudaMemset(B, 0, sizeof(R) * mesh.N2));
@@ -190,9 +191,10 @@ struct SimImpl final : SimBase {
         // particles, double-buffered for the re-sort
         for (int k = 0; k < 2; k++) {
             Particles<P> &p = parts[k];
-            if ((st = dalloc(p.tri, cap)) || (st = dalloc(p.l0, cap)) || (st = dalloc(p.l1, cap)) ||
-                (st = dalloc(p.ur, cap)) || (st = dalloc(p.up, cap)) || (st = dalloc(p.uz, cap)) ||
-                (st = dalloc(p.pid, cap)))
+            const int64_t ca = cap + SLOT_PAD;  // bulk copies round up to 16 bytes
+            if ((st = dalloc(p.tri, ca)) || (st = dalloc(p.l0, ca)) || (st = dalloc(p.l1, ca)) ||
+                (st = dalloc(p.ur, ca)) || (st = dalloc(p.up, ca)) || (st = dalloc(p.uz, ca)) ||
+                (st = dalloc(p.pid, ca)))
                 return st;
         }
         if ((st = dalloc(d_n, 1)) || (st = dalloc(counters, CNT_N))) return st;
@@ -258,6 +260,14 @@ struct SimImpl final : SimBase {
         a.nf = nf;
         a.dt = (R)dt;
         a.j_scale = j_scale();
+        a.node_ptr = dd.node_ptr;
+        a.node_edge = dd.node_edge;
+        a.node_sign = dd.node_sign;
+        a.Qn = nullptr;
+        a.Qabs = Qabs;
+        a.Qnext = nullptr;
+        a.counters = counters;
+        a.N0 = m->N0;
         return a;
     }
 
@@ -404,14 +414,17 @@ struct SimImpl final : SimBase {
         for (int64_t it = 0; it < n; it++) {
             if (dgl_dirty) {
                 // DGL reference res = D_div D^n - Q^n before the first step of this state
-                launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, D, dgl_ref, 1, E, B, mu_inv,
+                launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, D, dgl_ref, 1, E, B, mu_inv,
                                parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
                 dgl_dirty = false;
             }
             Acc *Qnext = Qbuf[1 - qcur];
             PIC_CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(Acc) * m->N1, s));
-            PIC_CUDA_TRY(cudaMemsetAsync(Qnext, 0, sizeof(Acc) * m->N0, s));
+            // FP32: Q^{n+1} is written whole by the per-node charge kernel
+            if constexpr (!P::fixed) PIC_CUDA_TRY(cudaMemsetAsync(Qnext, 0, sizeof(Acc) * m->N0, s));
             PIC_CUDA_TRY(cudaMemsetAsync(Qabs, 0, sizeof(Acc) * m->N0, s));
+            fa.Qn = Qn();
+            fa.Qnext = Qnext;
             launch_field_b<P>(fa, s);
             PushArgs<P> pa;
             pa.rec = rec;
@@ -476,7 +489,7 @@ struct SimImpl final : SimBase {
 
     pic_status diagnostics(pic_diag *o, double *Eo, double *Bo, double *Jo, cudaStream_t s) override {
         if (dgl_dirty) {
-            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, D, dgl_ref, 1, E, B, mu_inv,
+            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, D, dgl_ref, 1, E, B, mu_inv,
                            parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
             dgl_dirty = false;
         }
@@ -485,8 +498,18 @@ struct SimImpl final : SimBase {
         if (o) {
             PIC_CUDA_TRY(cudaMemsetAsync(diag_out, 0, sizeof(double) * 8, s));
             double inv_c2 = 1.0 / (m->units.c * m->units.c);
+            Acc *qp = nullptr;
+            if constexpr (P::fixed) {
+                // Eq. charge evaluated at the current positions, to check the carried Q
+                int64_t ns = 0;
+                pic_status st = read_count(&ns, s);
+                if (st != PIC_OK) return st;
+                PIC_CUDA_TRY(cudaMemsetAsync(qpos, 0, sizeof(Acc) * m->N0, s));
+                launch_deposit_q<P>(rec, parts[cur], 0, ns, qpos, s);
+                qp = qpos;
+            }
             // the last step wrote Q^{n+1} into Qn() and kept Q^n in the other buffer
-            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, D, dgl_ref, 0, E, B, mu_inv,
+            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, qp, D, dgl_ref, 0, E, B, mu_inv,
                            parts[cur], d_n, n_bound, q_scale(), inv_c2, diag_out, s);
             PIC_CUDA_TRY(cudaGetLastError());
             PIC_CUDA_TRY(cudaMemcpyAsync(out, diag_out, sizeof out, cudaMemcpyDeviceToHost, s));
@@ -512,6 +535,11 @@ struct SimImpl final : SimBase {
         }
         PIC_CUDA_TRY(cudaStreamSynchronize(s));
         if (jdev) release(jdev);
+        if (o && cnt[CNT_TIMEOUT]) {
+            set_error("pic_diagnostics: %llu bounded device waits timed out; the state is invalid",
+                      (unsigned long long)cnt[CNT_TIMEOUT]);
+            return PIC_ERR_TIMEOUT;
+        }
         if (o) {
             o->n_absorbed = (int64_t)cnt[CNT_ABSORBED];
             o->walk_overflows = (int64_t)cnt[CNT_OVERFLOW];
@@ -519,7 +547,7 @@ struct SimImpl final : SimBase {
             o->n_particles = n_injected - (int64_t)cnt[CNT_ABSORBED];
             o->n_steps = n_steps;
             o->dce_max = out[0];
-            o->dce_nonzero = (int64_t)out[1];
+            o->dce_nonzero = (int64_t)out[1] + (int64_t)cnt[CNT_REMAINDER];
             o->nr_dce_max = out[2];
             o->dgl_drift = out[3] / (out[4] > 0 ? out[4] : 1.0);
             o->field_energy = out[5];
