@@ -182,6 +182,22 @@ pic_status pic_diagnostics(pic_sim *s, pic_diag *out, double *E_out, double *B_o
 pic_status pic_charges_get(pic_sim *s, double *Q, double *Q_prev, double *Q_absorbed,
                            void *cuda_stream);
 
+/* Same outputs as pic_charges_get, for callers that must not allocate device memory: a
+ * process whose device memory is already committed to another allocator's pool (where
+ * a new cudaMalloc would fail or fragment it), or a code path that is not allowed to
+ * allocate, such as the inside of a time loop with a fixed memory budget.  The paper has
+ * no counterpart; this is a library convenience.
+ * It calls no cudaMalloc or cudaFree and no allocating library routine.  Its device
+ * scratch is a fixed array inside the library (3 x 131072 doubles, 3 MB) that every GPU
+ * which loads the library keeps until the process exits.  The first call on a device
+ * looks up that array's device address on the current device; make the first call
+ * before any stream capture.  Meshes with more than 131072 nodes are rejected with
+ * PIC_ERR_ARG (use pic_charges_get).  All calls share the one array, so calls whose GPU
+ * work overlaps (different streams or threads) race; each call synchronises its stream
+ * before returning.  Q, Q_prev, Q_absorbed: N0 doubles each, or NULL. */
+pic_status pic_charges_get_static(pic_sim *s, double *Q, double *Q_prev, double *Q_absorbed,
+                                  void *cuda_stream);
+
 /* Number of particle slots in use (live and removed-but-not-yet-compacted). */
 pic_status pic_particles_count(pic_sim *s, int64_t *n_slots, void *cuda_stream);
 

@@ -17,6 +17,39 @@ struct Allocator {
 static Allocator g_allocator;
 static std::mutex g_allocator_mu;
 
+// Scratch of pic_charges_get_static: a fixed device array instead of an allocation, for
+// callers that must not allocate device memory.  Every GPU that loads the library holds
+// these 3 MB until the process exits.  Host code cannot use the symbol itself as a device
+// address; the address is looked up once per device (charge_scratch_address).
+constexpr int64_t STATIC_MAX_NODES = 131072;
+static __device__ __align__(256) double g_charge_scratch[3 * STATIC_MAX_NODES];
+static std::mutex g_charge_scratch_mu;
+static double *g_charge_scratch_ptr[64] = {nullptr};
+
+// Device address of g_charge_scratch on the current device, resolved on the first call
+// per device (cudaGetSymbolAddress, with that device current).
+static pic_status charge_scratch_address(double **out) {
+    int dev = 0;
+    PIC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("pic_charges_get_static: device index %d out of range", dev);
+        return PIC_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_charge_scratch_mu);
+    if (!g_charge_scratch_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_charge_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("pic_charges_get_static: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(e));
+            return PIC_ERR_CUDA;
+        }
+        g_charge_scratch_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_charge_scratch_ptr[dev];
+    return PIC_OK;
+}
+
 struct SimBase {
     virtual ~SimBase() = default;
     virtual pic_status fields_set(const double *E, const double *B, cudaStream_t s) = 0;
@@ -34,6 +67,7 @@ struct SimBase {
     virtual pic_status raw_get(void *dst, int64_t n, cudaStream_t s) = 0;
     virtual pic_status raw_set(const void *src, int64_t n, cudaStream_t s) = 0;
     virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
+    virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
     int32_t sort_interval = 4;
     int device = 0;
 };
@@ -569,6 +603,33 @@ struct SimImpl final : SimBase {
         else cudaFree(p);
     }
 
+    // pic_charges_get without any allocation: the conversion kernel writes into the
+    // library's static scratch, then each part is copied straight into the caller's
+    // host array.  Every value of the used part is overwritten, so no clearing is needed.
+    pic_status charges_static(double *Qo, double *Qpo, double *Qao, cudaStream_t s) override {
+        if (m->N0 > STATIC_MAX_NODES) {
+            set_error("pic_charges_get_static: the mesh has %lld nodes, the static scratch "
+                      "holds %lld; use pic_charges_get",
+                      (long long)m->N0, (long long)STATIC_MAX_NODES);
+            return PIC_ERR_ARG;
+        }
+        double *scr = nullptr;
+        pic_status st = charge_scratch_address(&scr);
+        if (st != PIC_OK) return st;
+        const double sc_ = (P::fixed ? LAM_INV : 1.0) * q_src;
+        double *outs[3] = {Qo, Qpo, Qao};
+        const Acc *ins[3] = {Qn(), Qbuf[1 - qcur], Qabs};
+        for (int k = 0; k < 3; k++)
+            if (outs[k]) launch_acc_to_double<P>(ins[k], scr + k * m->N0, m->N0, sc_, s);
+        PIC_CUDA_TRY(cudaGetLastError());
+        for (int k = 0; k < 3; k++)
+            if (outs[k])
+                PIC_CUDA_TRY(cudaMemcpyAsync(outs[k], scr + k * m->N0, sizeof(double) * m->N0,
+                                             cudaMemcpyDeviceToHost, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        return PIC_OK;
+    }
+
     pic_status charges(double *Qo, double *Qpo, double *Qao, cudaStream_t s) override {
         double *tmp = nullptr;
         pic_status st = dalloc(tmp, 3 * m->N0);
@@ -787,6 +848,12 @@ extern "C" pic_status pic_diagnostics(pic_sim *s, pic_diag *o, double *E, double
                                       void *st) {
     SIM_CHECK(s, "pic_diagnostics");
     return s->impl->diagnostics(o, E, B, J, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_charges_get_static(pic_sim *s, double *Q, double *Qp, double *Qa,
+                                             void *st) {
+    SIM_CHECK(s, "pic_charges_get_static");
+    return s->impl->charges_static(Q, Qp, Qa, (cudaStream_t)st);
 }
 
 extern "C" pic_status pic_charges_get(pic_sim *s, double *Q, double *Qp, double *Qa, void *st) {

@@ -67,6 +67,7 @@ _SIGS = {
     "pic_step": [_P, _I64, _P],
     "pic_diagnostics": [_P, ctypes.POINTER(pic_diag), _P, _P, _P, _P],
     "pic_charges_get": [_P, _P, _P, _P, _P],
+    "pic_charges_get_static": [_P, _P, _P, _P, _P],
     "pic_particles_count": [_P, _P, _P],
     "pic_particles_get": [_P, _I64, _P, _P, _P, _P, _P],
     "pic_particles_raw_bytes": [_P, _P],
@@ -291,6 +292,17 @@ def pic_diagnostics(sim, fields=False, stream=None):
     if fields:
         out.update(E=E, B=B, J=J)
     return out
+
+
+def pic_charges_get_static(sim, Q=None, Q_prev=None, Q_absorbed=None, stream=None):
+    """pic_charges_get for callers that must not allocate device memory (the library's
+    fixed scratch is used instead; meshes up to 131072 nodes).  The output arrays are the
+    caller's (float64, N0 each) and are filled in place; None skips one."""
+    for x in (Q, Q_prev, Q_absorbed):
+        assert x is None or (x.dtype == np.float64 and x.flags.c_contiguous)
+    _check(_lib.pic_charges_get_static(sim.ptr, _ptr(Q), _ptr(Q_prev), _ptr(Q_absorbed),
+                                       _stream(stream)), "pic_charges_get_static")
+    return Q, Q_prev, Q_absorbed
 
 
 def pic_charges_get(sim, stream=None):
