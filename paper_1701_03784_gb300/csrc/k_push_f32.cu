@@ -40,9 +40,11 @@ constexpr int TWO23_BITS = 0x4B000000;
 
 constexpr int CW = 8;              // compute warps per CTA
 constexpr int PT = CW * 32;        // compute threads per CTA
-constexpr int NT = PT + 32;        // plus one walker warp
+constexpr int NT = PT + 32;        // plus one producer warp
 constexpr int ROUNDS = 2;          // slots per compute thread per tile
 constexpr int TILE = PT * ROUNDS;  // slots per tile
+constexpr int STAGES = 2;          // tile buffers in flight
+constexpr int QCAP = 128;          // ring entries per compute warp (at most 31 + 2*32 used)
 constexpr long long WAIT_LIMIT = 1LL << 20;  // bounded mbarrier polling
 
 // s in [0, 2^23): exactly (float)s * 2^-22
@@ -127,22 +129,43 @@ __device__ __forceinline__ Seg segment_end(float f0, float f1, float f2, float d
     return r;
 }
 
-// Eq. current of the segment s -> e on the three local edges, each oriented from its lower
-// to its higher node index (flags bit k: local edge k runs (k+1)%3 -> (k+2)%3)
+// Eq. current of a segment s -> e inside one triangle.  With the local edges oriented
+// counter-clockwise (edge 0: 1->2, 1: 2->0, 2: 0->1) the currents are
+//   A0 = s1 e2 - s2 e1,  A1 = s2 e0 - s0 e2,  A2 = s0 e1 - s1 e0,
+// and because s and e both sum to 2^22, the net outflow at each node is
+//   A2 - A1 = 2^22 (s0 - e0),  A0 - A2 = 2^22 (s1 - e1)   (the identity behind Eq. DCE).
+// So one 64-bit product pair (A1) and two 32-bit differences determine all three, also
+// after summing over particles of the same triangle.
+__device__ __forceinline__ void ccw_from(long long A1, int d0, int d1, long long &A0,
+                                         long long &A2) {
+    A2 = A1 + ((long long)d0 << LAM_BITS);
+    A0 = A2 + ((long long)d1 << LAM_BITS);
+}
+// the ccw currents with the global orientation of each edge applied (flags bit k: local
+// edge k runs (k+1)%3 -> (k+2)%3, i.e. from its lower to its higher node index)
+__device__ __forceinline__ void oriented(int flags, long long &A0, long long &A1, long long &A2) {
+    if (!(flags & 1)) A0 = -A0;
+    if (!(flags & 2)) A1 = -A1;
+    if (!(flags & 4)) A2 = -A2;
+}
 __device__ __forceinline__ void currents(int s0, int s1, int s2, const Seg &e, int flags,
                                          long long &J0, long long &J1, long long &J2) {
-    J0 = (long long)s1 * e.e2 - (long long)s2 * e.e1;
     J1 = (long long)s2 * e.e0 - (long long)s0 * e.e2;
-    J2 = (long long)s0 * e.e1 - (long long)s1 * e.e0;
-    if (!(flags & 1)) J0 = -J0;
-    if (!(flags & 2)) J1 = -J1;
-    if (!(flags & 4)) J2 = -J2;
+    ccw_from(J1, s0 - e.e0, s1 - e.e1, J0, J2);
+    oriented(flags, J0, J1, J2);
 }
 
 // a particle that reached edge kx of triangle t at the fixed-point point (s0, s1, 2^22 -
-// s0 - s1) and still moves by (d0, d1)
+// s0 - s1) and still moves by (d0, d1): an entry of the walker's queue
 struct QEntry {
     int slot, t, kx, s0, s1;
+    float d0, d1;
+};
+
+// a particle that enters triangle nb through the edge of nodes (ga, gb) with fixed-point
+// coordinates (va, 2^22 - va) there, and still moves by (d0, d1)
+struct NEntry {
+    int slot, nb, ga, gb, va;
     float d0, d1;
 };
 
@@ -157,12 +180,10 @@ struct __align__(128) TileBuf {
 };
 
 struct PushSmem {
-    TileBuf buf[2];
-    QEntry q[2][TILE];
-    unsigned long long tile_full[2];   // bulk copies of a tile landed
-    unsigned long long q_full[2];      // the compute warps filled a queue buffer
-    unsigned long long q_empty[2];     // the walker drained it
-    int qn[2];
+    TileBuf buf[STAGES];
+    QEntry q[CW][QCAP];                // per compute warp: ring of particles to walk on
+    unsigned long long full[STAGES];   // the bulk copies of a stage's tile landed
+    unsigned long long empty[STAGES];  // every compute warp released the stage
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -202,17 +223,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
 }
-// barrier of the compute warps only (named barrier 1), OR-reducing a flag
-__device__ __forceinline__ bool compute_sync_or(bool v) {
-    unsigned r;
-    asm volatile(
-        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, 1, %2, pi;\n"
-        " selp.u32 %0, 1, 0, po;\n}\n"
-        : "=r"(r) : "r"((unsigned)v), "n"(PT) : "memory");
-    return r != 0;
-}
-
-// thread 0: stage tile `tile` (slots [tile*TILE, tile*TILE + TILE) clipped to n, rounded up
+// producer lane: stage tile `tile` (slots [tile*TILE, tile*TILE + TILE) clipped to n, rounded up
 // to 4 slots so every copy is a multiple of 16 bytes; the arrays have that much room)
 __device__ __forceinline__ void issue_tile(const PushArgs<PF32> &a, PushSmem &sm, int stage,
                                            long long tile, long long n) {
@@ -220,7 +231,7 @@ __device__ __forceinline__ void issue_tile(const PushArgs<PF32> &a, PushSmem &sm
     const long long cnt = min((long long)TILE, n - base);
     const unsigned bytes = (unsigned)(((cnt + 3) & ~3LL) * 4);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    unsigned long long *bar = &sm.tile_full[stage];
+    unsigned long long *bar = &sm.full[stage];
     mbar_expect_tx(bar, 6 * bytes);
     TileBuf &b = sm.buf[stage];
     bulk_load(b.tri, a.p.tri + base, bytes, bar);
@@ -232,15 +243,16 @@ __device__ __forceinline__ void issue_tile(const PushArgs<PF32> &a, PushSmem &sm
 }
 
 // Gather, Boris, rotate-back and the first segment of one particle (slot i, state from the
-// staged tile).  Returns the first segment's three edge currents; a particle whose
-// segment reaches an edge is described in e and flagged.
+// staged tile).  Returns the first segment's current as (A1, s0 - e0, s1 - e1) (see
+// ccw_from) and the triangle's orientation flags; a particle whose segment reaches an
+// edge is described in e and flagged.
 __device__ __forceinline__ void push_first(const PushArgs<PF32> &a, int i, int t0, int s0,
-                                           int s1, float ur, float up, float uz, long long &j0a,
-                                           long long &j0b, long long &j0c, bool &crossed,
+                                           int s1, float ur, float up, float uz, long long &a1,
+                                           int &dq0, int &dq1, int &flags, bool &crossed,
                                            QEntry &e) {
     const float4 *R = rec4(a.rec, t0);
     const float4 G = __ldg(R + 0), RH = __ldg(R + 1), CA = __ldg(R + 2), CB = __ldg(R + 3);
-    const int flags = __ldg(&reinterpret_cast<const int *>(a.rec + t0)[4 * 4 + 3]);
+    flags = __ldg(&reinterpret_cast<const int *>(a.rec + t0)[4 * 4 + 3]);
     const int s2 = LAM_ONE - s0 - s1;
     const float f0 = fix2f(s0), f1 = fix2f(s1), f2 = fix2f(s2);
 
@@ -283,80 +295,112 @@ __device__ __forceinline__ void push_first(const PushArgs<PF32> &a, int i, int t
     __stcs(a.p.uz + i, uz);
 
     // first segment, in the start triangle (the whole path for most particles)
-    const float dl0 = G.x * d0 + G.y * d1, dl1 = G.z * d0 + G.w * d1;
-    const Seg sg = segment_end(f0, f1, f2, dl0, dl1, -(dl0 + dl1), -1);
-    currents(s0, s1, s2, sg, flags, j0a, j0b, j0c);
-    if (sg.kx < 0) {
-        __stcs(a.p.l0 + i, sg.e0);
-        __stcs(a.p.l1 + i, sg.e1);
+    const float dl0 = G.x * d0 + G.y * d1, dl1 = G.z * d0 + G.w * d1, dl2 = -(dl0 + dl1);
+    const float le0 = f0 + dl0, le1 = f1 + dl1, le2 = f2 + dl2;
+    if (le0 >= 0.f && le1 >= 0.f && le2 >= 0.f) {
+        // the end point lies in t0: round it to fixed point summing to 2^22 (a rounding
+        // deficit of the remainder goes to the larger of the other two coordinates)
+        int e0 = f2fix(le0), e1 = f2fix(le1);
+        int e2 = LAM_ONE - e0 - e1;
+        const int neg = min(e2, 0);
+        const bool big0 = e0 >= e1;
+        e0 += big0 ? neg : 0;
+        e1 += big0 ? 0 : neg;
+        e2 -= neg;
+        a1 = (long long)s2 * e0 - (long long)s0 * e2;
+        dq0 = s0 - e0;
+        dq1 = s1 - e1;
+        __stcs(a.p.l0 + i, e0);
+        __stcs(a.p.l1 + i, e1);
     } else {
+        const Seg sg = segment_end(f0, f1, f2, dl0, dl1, dl2, -1);
+        a1 = (long long)s2 * sg.e0 - (long long)s0 * sg.e2;
+        dq0 = s0 - sg.e0;
+        dq1 = s1 - sg.e1;
         crossed = true;
         e = QEntry{i, t0, sg.kx, sg.e0, sg.e1, d0 * (1.f - sg.sx), d1 * (1.f - sg.sx)};
     }
 }
 
-// Finish a particle that reached an edge: stop on the axis, leave at a wall or at the walk
-// cap (its charge goes to Q_abs), or enter the neighbour (the shared nodes keep their
-// coordinates) and deposit that segment's current, repeating across further edges.
-// Returns the number of crossings after the first.
-__device__ __forceinline__ unsigned walk_on(const PushArgs<PF32> &a, const QEntry &q) {
-    int t = q.t, kx = q.kx;
-    int s0 = q.s0, s1 = q.s1, s2 = LAM_ONE - q.s0 - q.s1;
-    float d0 = q.d0, d1 = q.d1;
-    int4 nd = __ldg(rec4i(a.rec, t) + 4);
-    int4 NB = __ldg(rec4i(a.rec, t) + 6);
+// The edge crossing that ends a segment in triangle t (nodes nd, neighbours NB) at the
+// fixed-point point (s0, s1, s2): stop on the axis, leave at a wall or at the walk cap
+// (its charge goes to Q_abs), or describe the entry into the neighbour in e.  Returns
+// true when the walk continues in the neighbour.
+__device__ __forceinline__ bool cross_edge(const PushArgs<PF32> &a, int slot, int t, int kx,
+                                           int ncross, int4 nd, int4 NB, int s0, int s1, int s2,
+                                           float d0, float d1, NEntry &e) {
+    const int nb = sel3(kx, NB.x, NB.y, NB.z);
+    if (nb < 0 && -nb == PIC_BC_AXIS) {
+        // the meridian segment stays at rho >= 0: it stops on the axis edge
+        __stcs(a.p.tri + slot, t);
+        __stcs(a.p.l0 + slot, s0);
+        __stcs(a.p.l1 + slot, s1);
+        return false;
+    }
+    if (nb < 0 || ncross + 1 >= a.walk_cap) {
+        red_add(a.Qabs + nd.x, s0);
+        red_add(a.Qabs + nd.y, s1);
+        red_add(a.Qabs + nd.z, s2);
+        if (nb >= 0) atomicAdd(a.counters + CNT_OVERFLOW, 1ULL);
+        atomicAdd(a.counters + CNT_ABSORBED, 1ULL);
+        __stcs(a.p.tri + slot, -1);
+        return false;
+    }
+    e = NEntry{slot, nb, sel3(kx, nd.y, nd.z, nd.x), sel3(kx, nd.z, nd.x, nd.y),
+               sel3(kx, s1, s2, s0), d0, d1};
+    return true;
+}
+
+// Enter the neighbour (the shared nodes keep their coordinates), deposit the segment's
+// current, and go on across further edges until the end point, the axis, a wall or the
+// cap.  Returns the number of crossings after the first.
+__device__ __forceinline__ unsigned walk_from(const PushArgs<PF32> &a, NEntry q) {
     unsigned cx = 0;
-    for (int ncross = 0;; ncross++) {
-        const int nb = sel3(kx, NB.x, NB.y, NB.z);
-        if (nb < 0 && -nb == PIC_BC_AXIS) {
-            // the meridian segment stays at rho >= 0: it stops on the axis edge
-            __stcs(a.p.tri + q.slot, t);
-            __stcs(a.p.l0 + q.slot, s0);
-            __stcs(a.p.l1 + q.slot, s1);
-            return cx;
-        }
-        if (nb < 0 || ncross + 1 >= a.walk_cap) {
-            red_add(a.Qabs + nd.x, s0);
-            red_add(a.Qabs + nd.y, s1);
-            red_add(a.Qabs + nd.z, s2);
-            if (nb >= 0) atomicAdd(a.counters + CNT_OVERFLOW, 1ULL);
-            atomicAdd(a.counters + CNT_ABSORBED, 1ULL);
-            __stcs(a.p.tri + q.slot, -1);
-            return cx;
-        }
-        const int ga = sel3(kx, nd.y, nd.z, nd.x), gb = sel3(kx, nd.z, nd.x, nd.y);
-        const int va = sel3(kx, s1, s2, s0), vb = sel3(kx, s2, s0, s1);
-        const float4 GN = __ldg(rec4(a.rec, nb));
-        const int4 NN = __ldg(rec4i(a.rec, nb) + 4);
-        const int4 EG = __ldg(rec4i(a.rec, nb) + 5);
-        NB = __ldg(rec4i(a.rec, nb) + 6);
-        s0 = NN.x == ga ? va : (NN.x == gb ? vb : 0);
-        s1 = NN.y == ga ? va : (NN.y == gb ? vb : 0);
-        s2 = NN.z == ga ? va : (NN.z == gb ? vb : 0);
-        const int entered = (NN.x != ga && NN.x != gb) ? 0 : ((NN.y != ga && NN.y != gb) ? 1 : 2);
-        t = nb;
-        nd = NN;
-        const float dl0 = GN.x * d0 + GN.y * d1, dl1 = GN.z * d0 + GN.w * d1;
-        const Seg sg = segment_end(fix2f(s0), fix2f(s1), fix2f(s2), dl0, dl1, -(dl0 + dl1), entered);
+    for (int ncross = 1;; ncross++) {
+        const int t = q.nb;
+        const float4 GN = __ldg(rec4(a.rec, t));
+        const int4 NN = __ldg(rec4i(a.rec, t) + 4);
+        const int4 EG = __ldg(rec4i(a.rec, t) + 5);
+        const int vb = LAM_ONE - q.va;
+        const int s0 = NN.x == q.ga ? q.va : (NN.x == q.gb ? vb : 0);
+        const int s1 = NN.y == q.ga ? q.va : (NN.y == q.gb ? vb : 0);
+        const int s2 = NN.z == q.ga ? q.va : (NN.z == q.gb ? vb : 0);
+        const int entered =
+            (NN.x != q.ga && NN.x != q.gb) ? 0 : ((NN.y != q.ga && NN.y != q.gb) ? 1 : 2);
+        const float dl0 = GN.x * q.d0 + GN.y * q.d1, dl1 = GN.z * q.d0 + GN.w * q.d1;
+        const Seg sg =
+            segment_end(fix2f(s0), fix2f(s1), fix2f(s2), dl0, dl1, -(dl0 + dl1), entered);
         long long J0, J1, J2;
         currents(s0, s1, s2, sg, NN.w, J0, J1, J2);
         red_add(a.J + EG.x, J0);
         red_add(a.J + EG.y, J1);
         red_add(a.J + EG.z, J2);
-        s0 = sg.e0;
-        s1 = sg.e1;
-        s2 = sg.e2;
         if (sg.kx < 0) {
             __stcs(a.p.tri + q.slot, t);
-            __stcs(a.p.l0 + q.slot, s0);
-            __stcs(a.p.l1 + q.slot, s1);
+            __stcs(a.p.l0 + q.slot, sg.e0);
+            __stcs(a.p.l1 + q.slot, sg.e1);
             return cx;
         }
         cx++;
-        kx = sg.kx;
-        d0 *= 1.f - sg.sx;
-        d1 *= 1.f - sg.sx;
+        const int4 NB = __ldg(rec4i(a.rec, t) + 6);
+        NEntry nx;
+        if (!cross_edge(a, q.slot, t, sg.kx, ncross, NN, NB, sg.e0, sg.e1, sg.e2,
+                        q.d0 * (1.f - sg.sx), q.d1 * (1.f - sg.sx), nx))
+            return cx;   // stopped on the axis, or removed
+        q = nx;
     }
+}
+
+// Finish a queued particle (it reached edge kx of triangle t): resolve the crossing, then
+// walk on.  Returns the number of crossings after the first.
+__device__ __forceinline__ unsigned walk_on(const PushArgs<PF32> &a, const QEntry &q) {
+    const int4 nd = __ldg(rec4i(a.rec, q.t) + 4);
+    const int4 NB = __ldg(rec4i(a.rec, q.t) + 6);
+    NEntry e;
+    if (!cross_edge(a, q.slot, q.t, q.kx, 0, nd, NB, q.s0, q.s1, LAM_ONE - q.s0 - q.s1, q.d0,
+                    q.d1, e))
+        return 0;
+    return walk_from(a, e);
 }
 
 }  // namespace
@@ -370,11 +414,9 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
     const unsigned full = 0xffffffffu;
     if ((long long)blockIdx.x >= ntiles) return;
     if (tid == 0) {
-        for (int s = 0; s < 2; s++) {
-            mbar_init(&sm.tile_full[s], 1);
-            mbar_init(&sm.q_full[s], CW);
-            mbar_init(&sm.q_empty[s], 1);
-            sm.qn[s] = 0;
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], CW);
         }
         mbar_fence_init();
     }
@@ -382,84 +424,85 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
     unsigned cx = 0;
 
     if (warp == CW) {
-        // ---- walker warp: drain the queue of tile k while the compute warps do tile k+1
-        int it = 0;
-        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
-            const int qb = it & 1;
-            const bool ok = mbar_wait(&sm.q_full[qb], (unsigned)(it >> 1) & 1u);
-            if (__any_sync(full, !ok)) {   // leave together
-                if (lane == 0) atomicAdd(a.counters + CNT_TIMEOUT, 1ULL);
-                break;
-            }
-            const int nq = sm.qn[qb];
-            for (int k = lane; k < nq; k += 32) cx += walk_on(a, sm.q[qb][k]);
-            __syncwarp();
-            if (lane == 0) {
-                sm.qn[qb] = 0;
-                mbar_arrive(&sm.q_empty[qb]);
+        // ---- producer warp: lane 0 stages the CTA's tiles; a stage is refilled once every
+        // compute warp has released its previous tile
+        if (lane == 0) {
+            long long it = 0;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+                const int stage = (int)(it % STAGES);
+                if (it >= STAGES &&
+                    !mbar_wait(&sm.empty[stage], (unsigned)((it / STAGES - 1) & 1))) {
+                    atomicAdd(a.counters + CNT_TIMEOUT, 1ULL);
+                    break;
+                }
+                issue_tile(a, sm, stage, tile, n);
             }
         }
     } else {
-        // ---- compute warps
-        if (tid == 0) issue_tile(a, sm, 0, blockIdx.x, n);
-        unsigned parity = 0;   // bit s: parity of the next completion of tile_full[s]
-        int stage = 0, it = 0;
+        // ---- compute warps.  Particles that reach an edge go to the warp's own ring of
+        // entries; whenever 32 are waiting the warp walks them on with all lanes.
+        QEntry *ring = sm.q[warp];
+        unsigned head = 0, tail = 0;   // warp-uniform, ring index = value & (QCAP - 1)
+        long long it = 0;
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
-            const long long next = tile + gridDim.x;
-            if (next < ntiles && tid == 0) issue_tile(a, sm, stage ^ 1, next, n);
-            const int qb = it & 1;
-            bool ok = it < 2 || mbar_wait(&sm.q_empty[qb], (unsigned)((it >> 1) - 1) & 1u);
-            ok = ok && mbar_wait(&sm.tile_full[stage], (parity >> stage) & 1u);
-            if (compute_sync_or(!ok)) {
-                if (tid == 0) {
-                    // let this CTA's bulk copies land before it leaves (bounded)
+            const int stage = (int)(it % STAGES);
+            const bool ok = mbar_wait(&sm.full[stage], (unsigned)((it / STAGES) & 1));
+            if (__any_sync(full, !ok)) {
+                if (lane == 0) {
+                    // give the stage's bulk copies one more bounded wait before leaving
                     atomicAdd(a.counters + CNT_TIMEOUT, 1ULL);
-                    mbar_wait(&sm.tile_full[stage], (parity >> stage) & 1u);
-                    if (next < ntiles) mbar_wait(&sm.tile_full[stage ^ 1], (parity >> (stage ^ 1)) & 1u);
+                    mbar_wait(&sm.full[stage], (unsigned)((it / STAGES) & 1));
                 }
                 break;
             }
-            parity ^= 1u << stage;
             const TileBuf &b = sm.buf[stage];
             const long long base = tile * TILE;
             for (int r = 0; r < ROUNDS; r++) {
                 const int k = r * PT + tid;
                 const long long i = base + k;
                 const int t0 = i < n ? b.tri[k] : -1;
-                long long j0a = 0, j0b = 0, j0c = 0;
+                long long a1 = 0;
+                int dq0 = 0, dq1 = 0, flags = 0;
                 bool crossed = false;
                 QEntry e;
                 if (t0 >= 0)
-                    push_first(a, (int)i, t0, b.l0[k], b.l1[k], b.ur[k], b.up[k], b.uz[k], j0a, j0b,
-                               j0c, crossed, e);
-                // first-segment currents: one set of atomics per start triangle per warp
+                    push_first(a, (int)i, t0, b.l0[k], b.l1[k], b.ur[k], b.up[k], b.uz[k], a1, dq0,
+                               dq1, flags, crossed, e);
+                // first-segment currents: summed over the lanes of each start triangle (one
+                // 64-bit and two 32-bit sums determine all three edges), one set of atomics
                 const unsigned grp = __match_any_sync(full, t0);
                 if (t0 >= 0) {
                     const int cnt = __popc(grp);
-                    const long long sa = group_sum(grp, cnt, j0a);
-                    const long long sb = group_sum(grp, cnt, j0b);
-                    const long long sc = group_sum(grp, cnt, j0c);
+                    long long S1 = group_sum(grp, cnt, a1);
+                    const int D0 = (int)__reduce_add_sync(grp, (unsigned)dq0);
+                    const int D1 = (int)__reduce_add_sync(grp, (unsigned)dq1);
                     if (lane == __ffs(grp) - 1) {
+                        long long S0, S2;
+                        ccw_from(S1, D0, D1, S0, S2);
+                        oriented(flags, S0, S1, S2);
                         const int4 EG = __ldg(rec4i(a.rec, t0) + 5);
-                        red_add(a.J + EG.x, sa);
-                        red_add(a.J + EG.y, sb);
-                        red_add(a.J + EG.z, sc);
+                        red_add(a.J + EG.x, S0);
+                        red_add(a.J + EG.y, S1);
+                        red_add(a.J + EG.z, S2);
                     }
                 }
-                // particles that reached an edge go to the walker's queue
+                // particles that reached an edge go to this warp's ring
                 const unsigned qmask = __ballot_sync(full, crossed);
                 cx += crossed ? 1u : 0u;
-                int qbase = 0;
-                if (lane == 0 && qmask) qbase = atomicAdd(&sm.qn[qb], __popc(qmask));
-                qbase = __shfl_sync(full, qbase, 0);
-                if (crossed) sm.q[qb][qbase + __popc(qmask & ((1u << lane) - 1))] = e;
+                if (crossed) ring[(tail + __popc(qmask & ((1u << lane) - 1))) & (QCAP - 1)] = e;
+                tail += __popc(qmask);
             }
+            // this warp is done reading the stage: release it to the producer
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.q_full[qb]);
-            // every compute warp is done with buffer `stage` before thread 0 refills it
-            compute_sync_or(false);
-            stage ^= 1;
+            if (lane == 0) mbar_arrive(&sm.empty[stage]);
+            while (tail - head >= 32) {
+                cx += walk_on(a, ring[(head + lane) & (QCAP - 1)]);
+                head += 32;
+                __syncwarp();
+            }
         }
+        // the rest of the ring (fewer than 32 entries)
+        if (lane < (int)(tail - head)) cx += walk_on(a, ring[(head + lane) & (QCAP - 1)]);
     }
     const unsigned sx = __reduce_add_sync(full, cx);
     if (lane == 0 && sx) atomicAdd(a.counters + CNT_CROSSINGS, (unsigned long long)sx);
