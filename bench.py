@@ -5,7 +5,7 @@ fixed-point positions and currents.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step is one full cycle of the method (B update, gather + Boris + walk + scatter,
-SPAI E update, re-sort every 4 steps).  Prints one JSON line (rank 0).  Under torchrun
+SPAI E update, re-sort every 16 steps).  Prints one JSON line (rank 0).  Under torchrun
 each rank runs an independent replica of the workload (the method's state does not
 shard without a domain decomposition): weak scaling, no collective on the data path.
 """
@@ -219,7 +219,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--particles", type=int, default=16_000_000)
-    ap.add_argument("--sort-interval", type=int, default=4)
+    ap.add_argument("--sort-interval", type=int, default=16)
     ap.add_argument("--dt", type=float, default=None)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -148,7 +148,7 @@ pic_status pic_spai_get(const pic_mesh *m, int32_t *free_edges, int64_t *indptr,
 pic_status pic_sim_create(pic_mesh *m, double dt, double bz_guide, int64_t max_particles,
                           pic_sim **out);
 
-/* Steps between particle re-sorts by triangle (default 4; 0 disables re-sorting). */
+/* Steps between particle re-sorts by triangle (default 16; 0 disables re-sorting). */
 pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
 
 /* Set E^n (N1 doubles; PEC entries are forced to 0) and B^{n-1/2} (N2 doubles); either

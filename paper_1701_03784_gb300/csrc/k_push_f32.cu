@@ -45,7 +45,8 @@ constexpr int ROUNDS = 2;          // slots per compute thread per tile
 constexpr int TILE = PT * ROUNDS;  // slots per tile
 constexpr int STAGES = 2;          // tile buffers in flight
 constexpr int QCAP = 128;          // ring entries per compute warp (at most 31 + 2*32 used)
-constexpr long long WAIT_LIMIT = 1LL << 20;  // bounded mbarrier polling
+constexpr unsigned WAIT_SLICE_NS = 100000;    // one bounded mbarrier poll sleeps <= 100 us
+constexpr long long WAIT_LIMIT = 1LL << 14;   // polls before a wait gives up (<= ~1.6 s)
 
 // s in [0, 2^23): exactly (float)s * 2^-22
 __device__ __forceinline__ float fix2f(int s) {
@@ -202,12 +203,14 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned b
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
                  "r"(bytes) : "memory");
 }
+// test for the phase; a waiting thread is suspended until the phase completes or the
+// suspend-time hint (ns) runs out, instead of spinning
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity) {
     unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+        : "=r"(ok) : "r"(smem_u32(b)), "r"(parity), "n"(WAIT_SLICE_NS) : "memory");
     return ok != 0;
 }
 // bounded wait for the phase of the given parity; false when the limit is reached

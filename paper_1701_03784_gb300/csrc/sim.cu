@@ -68,7 +68,7 @@ struct SimBase {
     virtual pic_status raw_set(const void *src, int64_t n, cudaStream_t s) = 0;
     virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
     virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
-    int32_t sort_interval = 4;
+    int32_t sort_interval = 16;
     int device = 0;
 };
 
