@@ -25,36 +25,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-EPS0 = 8.8541878128e-12
-MU0 = 1.25663706212e-6
-C0 = 299792458.0
-QE = -1.602176634e-19
-ME = 9.1093837015e-31
+from workloads.bwo import EPS0, MU0, C0, QE, ME, DT_BWO, bwo_edge_field  # noqa: E402
 METRIC = "particle-steps/s (gather+Boris+locate+scatter), batched runs/h vs plain, 1 GB300"
 BYTES_PER_PARTICLE = 48          # particle kernel: 24 B of state read + 24 B written
 CPU_SAMPLE = 160_000             # particles in the oracle's bounded sample
 PUSH_PROFILE = os.path.join(ROOT, "profiles", "k_push_bwo16m.txt")
-# time step of the workload: half the SPAI leapfrog limit of this mesh (1.77e-13 s),
-# c dt = 0.12 mean edge lengths
-DT_BWO = 8.8e-14
 
 
 def workload(n_particles, seed=2002):
-    """Single BWO: wall 1.5 cm + 0.4 cm sin(2 pi z / 1.67 cm), 12 periods, 3 cm guides;
-    ~200k triangles; annular beam rho in [0.85, 0.95] cm over the ripple section, 400 kV,
-    3 kA, thermal spread 1e-3 u_z; guide field B_z = 2.5 T; seeded small random E."""
-    import workloads as W
-    nodes, tris, be, bt = W.bwo_mesh(200_000, seed=1002)
-    R, z_end, (zs0, zs1) = W.bwo_wall()
-    z, r, ur, up, uz = W.bwo_beam(n_particles, z0=zs0, z1=zs1, voltage=400e3, seed=seed)
-    gamma = 1.0 + 400e3 / 510998.95
-    vz = C0 * math.sqrt(1.0 - 1.0 / gamma ** 2)
-    # beam charge in the ripple section, I L / v_z, shared by the macro-particles
-    weight = 3e3 * (zs1 - zs0) / vz / (abs(QE) * n_particles)
-    # self-field scale of the beam, E ~ lambda / (2 pi eps0 rho); seed 1e-3 of it
-    e_scale = 1e-3 * (3e3 / vz) / (2 * math.pi * EPS0 * 0.9e-2)
-    return dict(nodes=nodes, tris=tris, be=be, bt=bt, z=z, r=r, ur=ur, up=up, uz=uz,
-                weight=weight, e_scale=e_scale, bz=2.5)
+    """The single-BWO workload (workloads/bwo.py): ~200k triangles, annular 400 kV / 3 kA
+    beam of n_particles macro-particles, B_z = 2.5 T, seeded small random E."""
+    from workloads.bwo import bwo_workload
+    return bwo_workload(n_particles, seed=seed)
 
 
 def clock_sampler():
@@ -146,7 +128,7 @@ class OracleSample:
         self.OP = OP
         m = Mesh(wl["nodes"], wl["tris"], wl["be"], wl["bt"])
         self.pm = OP.PushMesh(m)
-        self.E = W.random_edge_values(m.N1, wl["e_scale"] * 2e-4, 7)
+        self.E = bwo_edge_field(m.N1, wl["e_scale"], 7)
         self.E[m.edge_tag == 1] = 0.0
         self.Bavg = np.zeros(m.N2)
         sl = slice(0, n_sample)
@@ -180,6 +162,18 @@ def cpu_baseline(wl, budget_s=15.0):
             "sample": "%d of %d beam particles, %d steps, same mesh, fields and dt; FP64 C "
                       "oracle particle loop (gather, Boris, walk, scatter), single thread; %d "
                       "live at end" % (s.n, len(wl["z"]), done, live)}
+
+
+def reduce_over_ranks(ms, e2e_ms, n_particles, n_slots, dist=None, device="cpu"):
+    """Whole-job figures of a weak-scaling run: the slowest rank's timed regions and the
+    work of all ranks (each rank advances its own replica)."""
+    import torch
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    c = torch.tensor([float(n_particles), float(n_slots)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
 
 
 def run_reference(args):
@@ -250,7 +244,7 @@ def main():
     sim = pic.pic_sim_create(mesh, dt, wl["bz"], args.particles + 1024)
     pic.pic_sim_set_sort_interval(sim, args.sort_interval)
     import workloads as W
-    E0 = W.random_edge_values(info["n_edges"], wl["e_scale"] * 2e-4, 7 + rank)
+    E0 = bwo_edge_field(info["n_edges"], wl["e_scale"], 7 + rank)
     pic.pic_fields_set(sim, E0, np.zeros(info["n_tris"]))
     pic.pic_particles_inject(sim, wl["z"], wl["r"], wl["ur"], wl["up"], wl["uz"], QE, ME,
                              wl["weight"])
@@ -302,15 +296,8 @@ def main():
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
-    # max over ranks of the timed regions
-    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
-    cnt = torch.tensor([float(n_live + n_end) / 2.0, float(n_slots)], dtype=torch.float64,
-                       device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-    ms, e2e_ms = t.tolist()
-    total_particles, total_slots = cnt.tolist()
+    (ms, e2e_ms), (total_particles, total_slots) = reduce_over_ranks(
+        ms, e2e_ms, 0.5 * (n_live + n_end), n_slots, dist, device="cuda")
     value = total_particles * args.steps / (ms * 1e-3)
     e2e_value = total_slots * args.e2e_steps / (e2e_ms * 1e-3)
 
