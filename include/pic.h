@@ -74,8 +74,11 @@ typedef struct {
     double c;          /* speed of light (used in gamma = sqrt(1 + |u|^2/c^2))      */
     int32_t precision; /* PIC_FP64 or PIC_FP32                                      */
     int32_t walk_cap;  /* edge crossings per particle per step before the particle
-                          is removed and counted as a walk overflow; 0 means 16     */
+                          is removed and counted as a walk overflow; 0 means 16,
+                          at most PIC_WALK_CAP_MAX (bounds every walk loop)         */
 } pic_units;
+
+#define PIC_WALK_CAP_MAX 4096
 
 typedef struct {
     int64_t n_particles;     /* live particles                                          */
@@ -110,7 +113,10 @@ pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_, void *ctx);
  * and D_div (N0 x N1), per-triangle geometry, the rho-weighted Hodge matrix star_eps
  * (Eq. dis_hodge_eps, App. B; exact integration) and the diagonal star_mu^-1
  * (Eq. dis_hodge_mu: rho_bar_f / (mu0 A_f)).  Host-only; no device memory yet.
- * Errors: PIC_ERR_ARG (null / non-positive sizes / rho < 0 / bad index), PIC_ERR_MESH. */
+ * The mesh must be conforming: an edge belongs to one or two triangles, and two triangles
+ * sharing an edge lie on opposite sides of it (either node order is accepted per triangle).
+ * Errors: PIC_ERR_ARG (null / non-positive sizes / rho < 0 / bad index), PIC_ERR_MESH
+ * (degenerate or overlapping triangles, an edge in three triangles, bad boundary list). */
 pic_status pic_mesh_create(const double *nodes_zr, int64_t n_nodes, const int32_t *tris,
                            int64_t n_tris, const int32_t *bedge_nodes,
                            const int32_t *bedge_tag, int64_t n_bedges, const pic_units *u,

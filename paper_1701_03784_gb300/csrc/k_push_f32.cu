@@ -10,17 +10,19 @@
 // from the positions and compare).
 //
 // Work split (persistent CTAs, warp-specialised):
-//  * thread 0 stages tiles of TILE slots (structure of arrays, sorted by triangle) into
-//    shared memory with 1-D bulk copies on an mbarrier, double-buffered;
-//  * 8 compute warps advance two slots per thread per tile: gather, Boris, rotate-back
-//    and the first segment of the walk (the whole path for most particles).  The first
-//    segment's edge currents are summed over the lanes that share a start triangle
-//    (match.any, then redux.sync on two 23-bit limbs) and one lane per triangle issues
-//    the atomics.  A particle whose first segment reaches an edge is put in the tile's
-//    crossing queue in shared memory;
-//  * 1 walker warp finishes the queued particles of tile k (boundary, neighbour entry,
-//    further segments with direct atomics) while the compute warps work on tile k+1.
-//    The two queue buffers are handed over with full/empty mbarriers.
+//  * one producer warp (lane 0) stages tiles of TILE slots (structure of arrays, sorted
+//    by triangle) into shared memory with 1-D bulk copies, STAGES buffers deep; a
+//    buffer is refilled once all compute warps have arrived on its "empty" mbarrier;
+//  * 8 compute warps advance two slots per thread per tile, branch-free: gather, Boris,
+//    rotate-back and the end point in the start triangle.  For the ~4 in 5 particles
+//    whose end point stays there, the edge currents are summed over the lanes that
+//    share the triangle (match.any, then redux.sync on two 23-bit limbs) and one lane
+//    per triangle issues the atomics.  A particle that leaves its triangle is appended,
+//    with its start point and displacement, to its warp's ring in shared memory;
+//  * whenever 32 entries are waiting, the warp walks them with all lanes: per triangle
+//    the segment to the first edge reached, its currents (direct atomics), then the
+//    neighbour (entered through a precomputed local edge index) until the end point,
+//    the axis, a wall or the walk cap.  The remainder (< 32) is walked at the end.
 // Every wait is bounded: on timeout the error counter is set and the CTA leaves after a
 // bounded wait for its own bulk copy in flight.  Small arrays are indexed statically
 // (nothing in local memory); fixed <-> float conversions use exact magic-number
@@ -44,7 +46,7 @@ constexpr int NT = PT + 32;        // plus one producer warp
 constexpr int ROUNDS = 2;          // slots per compute thread per tile
 constexpr int TILE = PT * ROUNDS;  // slots per tile
 constexpr int STAGES = 2;          // tile buffers in flight
-constexpr int QCAP = 128;          // ring entries per compute warp (at most 31 + 2*32 used)
+constexpr int QCAP = 64;           // ring entries per compute warp (at most 31 + 32 used)
 constexpr unsigned WAIT_SLICE_NS = 100000;    // one bounded mbarrier poll sleeps <= 100 us
 constexpr long long WAIT_LIMIT = 1LL << 14;   // polls before a wait gives up (<= ~1.6 s)
 
@@ -65,7 +67,7 @@ __device__ __forceinline__ const int4 *rec4i(const TriRec<float> *rec, int t) {
 }
 
 __device__ __forceinline__ void red_add(unsigned long long *p, long long v) {
-    if (v != 0) atomicAdd(p, (unsigned long long)v);
+    atomicAdd(p, (unsigned long long)v);
 }
 
 // Sum a signed value |v| < 2^45 over the lanes of grp: redux.sync on the two 23-bit limbs
@@ -149,6 +151,8 @@ __device__ __forceinline__ void oriented(int flags, long long &A0, long long &A1
     if (!(flags & 2)) A1 = -A1;
     if (!(flags & 4)) A2 = -A2;
 }
+
+// the three oriented currents of one segment s -> e
 __device__ __forceinline__ void currents(int s0, int s1, int s2, const Seg &e, int flags,
                                          long long &J0, long long &J1, long long &J2) {
     J1 = (long long)s2 * e.e0 - (long long)s0 * e.e2;
@@ -156,18 +160,12 @@ __device__ __forceinline__ void currents(int s0, int s1, int s2, const Seg &e, i
     oriented(flags, J0, J1, J2);
 }
 
-// a particle that reached edge kx of triangle t at the fixed-point point (s0, s1, 2^22 -
-// s0 - s1) and still moves by (d0, d1): an entry of the walker's queue
-struct QEntry {
-    int slot, t, kx, s0, s1;
-    float d0, d1;
-};
-
-// a particle that enters triangle nb through the edge of nodes (ga, gb) with fixed-point
-// coordinates (va, 2^22 - va) there, and still moves by (d0, d1)
-struct NEntry {
-    int slot, nb, ga, gb, va;
-    float d0, d1;
+// a particle whose displacement leaves its start triangle t: slot, start point (s0, s1,
+// 2^22 - s0 - s1), meridian displacement (d0, d1) and its image (dl0, dl1) in t's
+// barycentric coordinates
+struct __align__(16) QEntry {
+    int slot, t, s0, s1;
+    float d0, d1, dl0, dl1;
 };
 
 // one tile of the structure-of-arrays particle state, staged by bulk copies
@@ -245,14 +243,15 @@ __device__ __forceinline__ void issue_tile(const PushArgs<PF32> &a, PushSmem &sm
     bulk_load(b.uz, a.p.uz + base, bytes, bar);
 }
 
-// Gather, Boris, rotate-back and the first segment of one particle (slot i, state from the
-// staged tile).  Returns the first segment's current as (A1, s0 - e0, s1 - e1) (see
-// ccw_from) and the triangle's orientation flags; a particle whose segment reaches an
-// edge is described in e and flagged.
-__device__ __forceinline__ void push_first(const PushArgs<PF32> &a, int i, int t0, int s0,
-                                           int s1, float ur, float up, float uz, long long &a1,
-                                           int &dq0, int &dq1, int &flags, bool &crossed,
-                                           QEntry &e) {
+// Gather, Boris, rotate-back and the end of the move for one particle (slot i, state from
+// the staged tile).  A particle whose end point stays in its start triangle t0 gets its
+// current as (A1, s0 - e0, s1 - e1) (see ccw_from) and its new position stored; one that
+// leaves t0 is described in e, flagged, and contributes no current here (its whole path,
+// the part in t0 included, is walked later).
+__device__ __forceinline__ void push_particle(const PushArgs<PF32> &a, int i, int t0, int s0,
+                                              int s1, float ur, float up, float uz,
+                                              long long &a1, int &dq0, int &dq1, int &flags,
+                                              bool &crossed, QEntry &e) {
     const float4 *R = rec4(a.rec, t0);
     const float4 G = __ldg(R + 0), RH = __ldg(R + 1), CA = __ldg(R + 2), CB = __ldg(R + 3);
     flags = __ldg(&reinterpret_cast<const int *>(a.rec + t0)[4 * 4 + 3]);
@@ -297,113 +296,129 @@ __device__ __forceinline__ void push_first(const PushArgs<PF32> &a, int i, int t
     __stcs(a.p.up + i, up);
     __stcs(a.p.uz + i, uz);
 
-    // first segment, in the start triangle (the whole path for most particles)
-    const float dl0 = G.x * d0 + G.y * d1, dl1 = G.z * d0 + G.w * d1, dl2 = -(dl0 + dl1);
-    const float le0 = f0 + dl0, le1 = f1 + dl1, le2 = f2 + dl2;
-    if (le0 >= 0.f && le1 >= 0.f && le2 >= 0.f) {
-        // the end point lies in t0: round it to fixed point summing to 2^22 (a rounding
-        // deficit of the remainder goes to the larger of the other two coordinates)
-        int e0 = f2fix(le0), e1 = f2fix(le1);
-        int e2 = LAM_ONE - e0 - e1;
-        const int neg = min(e2, 0);
-        const bool big0 = e0 >= e1;
-        e0 += big0 ? neg : 0;
-        e1 += big0 ? 0 : neg;
-        e2 -= neg;
-        a1 = (long long)s2 * e0 - (long long)s0 * e2;
-        dq0 = s0 - e0;
-        dq1 = s1 - e1;
+    // end point in barycentric coordinates of t0
+    const float dl0 = G.x * d0 + G.y * d1, dl1 = G.z * d0 + G.w * d1;
+    const float le0 = f0 + dl0, le1 = f1 + dl1, le2 = f2 - (dl0 + dl1);
+    crossed = !(le0 >= 0.f && le1 >= 0.f && le2 >= 0.f);
+    // inside t0: round to fixed point summing to 2^22 (a rounding deficit of the remainder
+    // goes to the larger of the other two coordinates).  A particle that leaves keeps
+    // e = s here, i.e. zero current.
+    int e0 = f2fix(le0), e1 = f2fix(le1);
+    int e2 = LAM_ONE - e0 - e1;
+    const int neg = min(e2, 0);
+    const bool big0 = e0 >= e1;
+    e0 += big0 ? neg : 0;
+    e1 += big0 ? 0 : neg;
+    e2 -= neg;
+    if (crossed) {
+        e0 = s0;
+        e1 = s1;
+        e2 = s2;
+    }
+    a1 = (long long)s2 * e0 - (long long)s0 * e2;
+    dq0 = s0 - e0;
+    dq1 = s1 - e1;
+    if (!crossed) {
         __stcs(a.p.l0 + i, e0);
         __stcs(a.p.l1 + i, e1);
-    } else {
-        const Seg sg = segment_end(f0, f1, f2, dl0, dl1, dl2, -1);
+    }
+    e = QEntry{i, t0, s0, s1, d0, d1, dl0, dl1};
+}
+
+__device__ __forceinline__ void store_position(const PushArgs<PF32> &a, int slot, int t, int e0,
+                                               int e1) {
+    __stcs(a.p.tri + slot, t);
+    __stcs(a.p.l0 + slot, e0);
+    __stcs(a.p.l1 + slot, e1);
+}
+
+// Walk the particles of one ring pass (all 32 lanes call this; lanes with valid = false
+// only take part in the warp-wide steps).  Per triangle: the segment to the end point or
+// to the first edge reached, its Eq. current, then the neighbour across that edge, where
+// the two shared nodes keep their coordinates.  The first segments lie in the triangles
+// the particles started in, which the lanes of a pass mostly share: their currents are
+// summed per triangle like those of the particles that stay; later segments deposit with
+// direct atomics.  The walk stops on the axis (the meridian segment stays at rho >= 0)
+// and removes the particle at a wall or at the walk cap (its charge goes to Q_abs).
+// Returns the number of edges reached.
+__device__ __forceinline__ unsigned walk_pass(const PushArgs<PF32> &a, const QEntry q, bool valid,
+                                              int lane) {
+    const unsigned full = 0xffffffffu;
+    int t = valid ? q.t : -1;
+    int s0 = q.s0, s1 = q.s1, s2 = LAM_ONE - q.s0 - q.s1;
+    int4 EG = make_int4(0, 0, 0, 0), NB = EG;
+    Seg sg{};
+    long long a1 = 0;
+    int dq0 = 0, dq1 = 0;
+    if (valid) {
+        EG = __ldg(rec4i(a.rec, t) + 5);   // edges, orientation flags
+        NB = __ldg(rec4i(a.rec, t) + 6);   // neighbours, entry indices
+        sg = segment_end(fix2f(s0), fix2f(s1), fix2f(s2), q.dl0, q.dl1, -(q.dl0 + q.dl1), -1);
         a1 = (long long)s2 * sg.e0 - (long long)s0 * sg.e2;
         dq0 = s0 - sg.e0;
         dq1 = s1 - sg.e1;
-        crossed = true;
-        e = QEntry{i, t0, sg.kx, sg.e0, sg.e1, d0 * (1.f - sg.sx), d1 * (1.f - sg.sx)};
     }
-}
-
-// The edge crossing that ends a segment in triangle t (nodes nd, neighbours NB) at the
-// fixed-point point (s0, s1, s2): stop on the axis, leave at a wall or at the walk cap
-// (its charge goes to Q_abs), or describe the entry into the neighbour in e.  Returns
-// true when the walk continues in the neighbour.
-__device__ __forceinline__ bool cross_edge(const PushArgs<PF32> &a, int slot, int t, int kx,
-                                           int ncross, int4 nd, int4 NB, int s0, int s1, int s2,
-                                           float d0, float d1, NEntry &e) {
-    const int nb = sel3(kx, NB.x, NB.y, NB.z);
-    if (nb < 0 && -nb == PIC_BC_AXIS) {
-        // the meridian segment stays at rho >= 0: it stops on the axis edge
-        __stcs(a.p.tri + slot, t);
-        __stcs(a.p.l0 + slot, s0);
-        __stcs(a.p.l1 + slot, s1);
-        return false;
+    const unsigned grp = __match_any_sync(full, t);
+    if (!valid) return 0;
+    {
+        const int cnt = __popc(grp);
+        long long S1 = group_sum(grp, cnt, a1);
+        const int D0 = (int)__reduce_add_sync(grp, (unsigned)dq0);
+        const int D1 = (int)__reduce_add_sync(grp, (unsigned)dq1);
+        if (lane == __ffs(grp) - 1) {
+            long long S0, S2;
+            ccw_from(S1, D0, D1, S0, S2);
+            oriented(EG.w, S0, S1, S2);
+            red_add(a.J + EG.x, S0);
+            red_add(a.J + EG.y, S1);
+            red_add(a.J + EG.z, S2);
+        }
     }
-    if (nb < 0 || ncross + 1 >= a.walk_cap) {
-        red_add(a.Qabs + nd.x, s0);
-        red_add(a.Qabs + nd.y, s1);
-        red_add(a.Qabs + nd.z, s2);
-        if (nb >= 0) atomicAdd(a.counters + CNT_OVERFLOW, 1ULL);
-        atomicAdd(a.counters + CNT_ABSORBED, 1ULL);
-        __stcs(a.p.tri + slot, -1);
-        return false;
-    }
-    e = NEntry{slot, nb, sel3(kx, nd.y, nd.z, nd.x), sel3(kx, nd.z, nd.x, nd.y),
-               sel3(kx, s1, s2, s0), d0, d1};
-    return true;
-}
-
-// Enter the neighbour (the shared nodes keep their coordinates), deposit the segment's
-// current, and go on across further edges until the end point, the axis, a wall or the
-// cap.  Returns the number of crossings after the first.
-__device__ __forceinline__ unsigned walk_from(const PushArgs<PF32> &a, NEntry q) {
-    unsigned cx = 0;
-    for (int ncross = 1;; ncross++) {
-        const int t = q.nb;
-        const float4 GN = __ldg(rec4(a.rec, t));
-        const int4 NN = __ldg(rec4i(a.rec, t) + 4);
-        const int4 EG = __ldg(rec4i(a.rec, t) + 5);
-        const int vb = LAM_ONE - q.va;
-        const int s0 = NN.x == q.ga ? q.va : (NN.x == q.gb ? vb : 0);
-        const int s1 = NN.y == q.ga ? q.va : (NN.y == q.gb ? vb : 0);
-        const int s2 = NN.z == q.ga ? q.va : (NN.z == q.gb ? vb : 0);
-        const int entered =
-            (NN.x != q.ga && NN.x != q.gb) ? 0 : ((NN.y != q.ga && NN.y != q.gb) ? 1 : 2);
-        const float dl0 = GN.x * q.d0 + GN.y * q.d1, dl1 = GN.z * q.d0 + GN.w * q.d1;
-        const Seg sg =
-            segment_end(fix2f(s0), fix2f(s1), fix2f(s2), dl0, dl1, -(dl0 + dl1), entered);
+    float d0 = q.d0, d1 = q.d1;
+    for (int ncross = 0;; ncross++) {
+        if (sg.kx < 0) {
+            store_position(a, q.slot, t, sg.e0, sg.e1);
+            return (unsigned)ncross;
+        }
+        const int kx = sg.kx;
+        const int nb = sel3(kx, NB.x, NB.y, NB.z);
+        if (nb < 0 && -nb == PIC_BC_AXIS) {
+            store_position(a, q.slot, t, sg.e0, sg.e1);
+            return (unsigned)ncross + 1;
+        }
+        if (nb < 0 || ncross + 1 >= a.walk_cap) {
+            const int4 nd = __ldg(rec4i(a.rec, t) + 4);
+            red_add(a.Qabs + nd.x, sg.e0);
+            red_add(a.Qabs + nd.y, sg.e1);
+            red_add(a.Qabs + nd.z, sg.e2);
+            if (nb >= 0) atomicAdd(a.counters + CNT_OVERFLOW, 1ULL);
+            atomicAdd(a.counters + CNT_ABSORBED, 1ULL);
+            __stcs(a.p.tri + q.slot, -1);
+            return (unsigned)ncross + 1;
+        }
+        // enter nb through its local edge j (opposite its node j): its node j+2 is node kx+1
+        // of t, its node j+1 is node kx+2
+        const int j = (NB.w >> (2 * kx)) & 3;
+        const int ea = sel3(kx, sg.e1, sg.e2, sg.e0);
+        const int eb = sel3(kx, sg.e2, sg.e0, sg.e1);
+        s0 = j == 0 ? 0 : (j == 1 ? ea : eb);
+        s1 = j == 1 ? 0 : (j == 2 ? ea : eb);
+        s2 = j == 2 ? 0 : (j == 0 ? ea : eb);
+        const float rest = 1.f - sg.sx;
+        d0 *= rest;
+        d1 *= rest;
+        t = nb;
+        const float4 G = __ldg(rec4(a.rec, t));
+        EG = __ldg(rec4i(a.rec, t) + 5);
+        NB = __ldg(rec4i(a.rec, t) + 6);
+        const float dl0 = G.x * d0 + G.y * d1, dl1 = G.z * d0 + G.w * d1;
+        sg = segment_end(fix2f(s0), fix2f(s1), fix2f(s2), dl0, dl1, -(dl0 + dl1), j);
         long long J0, J1, J2;
-        currents(s0, s1, s2, sg, NN.w, J0, J1, J2);
+        currents(s0, s1, s2, sg, EG.w, J0, J1, J2);
         red_add(a.J + EG.x, J0);
         red_add(a.J + EG.y, J1);
         red_add(a.J + EG.z, J2);
-        if (sg.kx < 0) {
-            __stcs(a.p.tri + q.slot, t);
-            __stcs(a.p.l0 + q.slot, sg.e0);
-            __stcs(a.p.l1 + q.slot, sg.e1);
-            return cx;
-        }
-        cx++;
-        const int4 NB = __ldg(rec4i(a.rec, t) + 6);
-        NEntry nx;
-        if (!cross_edge(a, q.slot, t, sg.kx, ncross, NN, NB, sg.e0, sg.e1, sg.e2,
-                        q.d0 * (1.f - sg.sx), q.d1 * (1.f - sg.sx), nx))
-            return cx;   // stopped on the axis, or removed
-        q = nx;
     }
-}
-
-// Finish a queued particle (it reached edge kx of triangle t): resolve the crossing, then
-// walk on.  Returns the number of crossings after the first.
-__device__ __forceinline__ unsigned walk_on(const PushArgs<PF32> &a, const QEntry &q) {
-    const int4 nd = __ldg(rec4i(a.rec, q.t) + 4);
-    const int4 NB = __ldg(rec4i(a.rec, q.t) + 6);
-    NEntry e;
-    if (!cross_edge(a, q.slot, q.t, q.kx, 0, nd, NB, q.s0, q.s1, LAM_ONE - q.s0 - q.s1, q.d0,
-                    q.d1, e))
-        return 0;
-    return walk_from(a, e);
 }
 
 }  // namespace
@@ -415,7 +430,11 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
     const long long ntiles = (n + TILE - 1) / TILE;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned full = 0xffffffffu;
-    if ((long long)blockIdx.x >= ntiles) return;
+    // each CTA takes a contiguous range of tiles: consecutive tiles hold neighbouring
+    // triangles (slots are sorted by triangle), so their records stay in this SM's L1
+    const long long per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const long long tile0 = (long long)blockIdx.x * per, tile1 = min(ntiles, tile0 + per);
+    if (tile0 >= tile1) return;
     if (tid == 0) {
         for (int s = 0; s < STAGES; s++) {
             mbar_init(&sm.full[s], 1);
@@ -431,7 +450,7 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
         // compute warp has released its previous tile
         if (lane == 0) {
             long long it = 0;
-            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+            for (long long tile = tile0; tile < tile1; tile++, it++) {
                 const int stage = (int)(it % STAGES);
                 if (it >= STAGES &&
                     !mbar_wait(&sm.empty[stage], (unsigned)((it / STAGES - 1) & 1))) {
@@ -442,12 +461,13 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
             }
         }
     } else {
-        // ---- compute warps.  Particles that reach an edge go to the warp's own ring of
-        // entries; whenever 32 are waiting the warp walks them on with all lanes.
+        // ---- compute warps.  Particles that leave their start triangle go to the warp's
+        // own ring; whenever 32 are waiting the warp walks them with all lanes.
         QEntry *ring = sm.q[warp];
+        const unsigned below = (1u << lane) - 1;
         unsigned head = 0, tail = 0;   // warp-uniform, ring index = value & (QCAP - 1)
         long long it = 0;
-        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+        for (long long tile = tile0; tile < tile1; tile++, it++) {
             const int stage = (int)(it % STAGES);
             const bool ok = mbar_wait(&sm.full[stage], (unsigned)((it / STAGES) & 1));
             if (__any_sync(full, !ok)) {
@@ -469,10 +489,11 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
                 bool crossed = false;
                 QEntry e;
                 if (t0 >= 0)
-                    push_first(a, (int)i, t0, b.l0[k], b.l1[k], b.ur[k], b.up[k], b.uz[k], a1, dq0,
-                               dq1, flags, crossed, e);
-                // first-segment currents: summed over the lanes of each start triangle (one
-                // 64-bit and two 32-bit sums determine all three edges), one set of atomics
+                    push_particle(a, (int)i, t0, b.l0[k], b.l1[k], b.ur[k], b.up[k], b.uz[k], a1,
+                                  dq0, dq1, flags, crossed, e);
+                // currents of the particles that stay: summed over the lanes of each start
+                // triangle (one 64-bit and two 32-bit sums determine all three edges), one
+                // set of atomics per triangle
                 const unsigned grp = __match_any_sync(full, t0);
                 if (t0 >= 0) {
                     const int cnt = __popc(grp);
@@ -489,23 +510,24 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
                         red_add(a.J + EG.z, S2);
                     }
                 }
-                // particles that reached an edge go to this warp's ring
+                // particles that leave go to this warp's ring (at most 31 + 32 entries)
                 const unsigned qmask = __ballot_sync(full, crossed);
-                cx += crossed ? 1u : 0u;
-                if (crossed) ring[(tail + __popc(qmask & ((1u << lane) - 1))) & (QCAP - 1)] = e;
+                if (crossed) ring[(tail + __popc(qmask & below)) & (QCAP - 1)] = e;
                 tail += __popc(qmask);
+                if (tail - head >= 32) {
+                    __syncwarp();
+                    cx += walk_pass(a, ring[(head + lane) & (QCAP - 1)], true, lane);
+                    head += 32;
+                    __syncwarp();
+                }
             }
             // this warp is done reading the stage: release it to the producer
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.empty[stage]);
-            while (tail - head >= 32) {
-                cx += walk_on(a, ring[(head + lane) & (QCAP - 1)]);
-                head += 32;
-                __syncwarp();
-            }
         }
         // the rest of the ring (fewer than 32 entries)
-        if (lane < (int)(tail - head)) cx += walk_on(a, ring[(head + lane) & (QCAP - 1)]);
+        __syncwarp();
+        cx += walk_pass(a, ring[(head + lane) & (QCAP - 1)], lane < (int)(tail - head), lane);
     }
     const unsigned sx = __reduce_add_sync(full, cx);
     if (lane == 0 && sx) atomicAdd(a.counters + CNT_CROSSINGS, (unsigned long long)sx);

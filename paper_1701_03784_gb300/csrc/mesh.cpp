@@ -173,7 +173,8 @@ extern "C" pic_status pic_mesh_create(const double *nodes_zr, int64_t n_nodes,
         return PIC_ERR_ARG;
     }
     if (!(u->eps0 > 0) || !(u->mu0 > 0) || !(u->c > 0) ||
-        (u->precision != PIC_FP64 && u->precision != PIC_FP32) || u->walk_cap < 0) {
+        (u->precision != PIC_FP64 && u->precision != PIC_FP32) || u->walk_cap < 0 ||
+        u->walk_cap > PIC_WALK_CAP_MAX) {
         set_error("pic_mesh_create: bad units");
         return PIC_ERR_ARG;
     }
@@ -262,6 +263,14 @@ extern "C" pic_status pic_mesh_create(const double *nodes_zr, int64_t n_nodes,
         }
         if (j - i == 2) {
             int64_t t0 = keys[i].second / 3, t1 = keys[i + 1].second / 3;
+            // both triangles are counter-clockwise: a conforming pair runs the shared edge in
+            // opposite directions; the same direction means they overlap
+            if (m.edge_face_sign[2 * e] == m.edge_face_sign[2 * e + 1]) {
+                set_error("pic_mesh_create: triangles %lld and %lld overlap at a shared edge",
+                          (long long)t0, (long long)t1);
+                delete pm;
+                return PIC_ERR_MESH;
+            }
             m.tri_nbr[keys[i].second] = (int32_t)t1;
             m.tri_nbr[keys[i + 1].second] = (int32_t)t0;
         }

@@ -123,9 +123,12 @@ struct alignas(sizeof(R) == 4 ? 128 : 64) TriRec {
     int32_t node[3];
     int32_t flags; // bit k: local edge k runs (k+1)%3 -> (k+2)%3 (D_curl entry +1)
     int32_t edge[3];
-    int32_t pad2;
+    int32_t eflags; // = flags, beside the edges: one 16-byte load gives both
     int32_t nbr[3]; // neighbour triangle, or -(PIC_BC_* tag) on the boundary
-    int32_t pad3;
+    int32_t entry;  // bits 2k, 2k+1: local index, in nbr[k], of the node opposite the
+                    // shared edge (the mesh is conforming and counter-clockwise, so the
+                    // neighbour runs that edge the other way: its node entry+1 is this
+                    // triangle's node k+2, its node entry+2 is node k+1)
 };
 
 struct PF32 {

@@ -176,6 +176,18 @@ struct SimImpl final : SimBase {
                 if (mesh.tri[3 * t + (k + 1) % 3] < mesh.tri[3 * t + (k + 2) % 3]) flags |= 1 << k;
             }
             x.flags = flags;
+            x.eflags = flags;
+            int entry = 0;
+            for (int k = 0; k < 3; k++) {
+                const int32_t nb = mesh.tri_nbr[3 * t + k];
+                if (nb < 0) continue;
+                const int32_t ga = mesh.tri[3 * t + (k + 1) % 3], gb = mesh.tri[3 * t + (k + 2) % 3];
+                for (int j = 0; j < 3; j++) {
+                    const int32_t q = mesh.tri[3 * nb + j];
+                    if (q != ga && q != gb) entry |= j << (2 * k);
+                }
+            }
+            x.entry = entry;
             x.inv_area = (R)(1.0 / mesh.area[t]);
         }
         if ((st = upload(rec, hr)) != PIC_OK) return st;

@@ -58,6 +58,14 @@ def test_bad_meshes_are_rejected(pic):
     with pytest.raises(pic.PicError) as e:
         pic.pic_mesh_create(nodes, tris, np.vstack([be, [[0, 2]]]), np.append(bt, 1))
     assert e.value.status == pic.PIC_ERR_MESH                     # interior edge listed
+    folded = np.vstack([nodes, [[0.6, 0.8]]])                     # both triangles below 0-2
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mesh_create(folded, np.array([[0, 1, 2], [0, 4, 2]]),
+                            np.array([[0, 1], [1, 2], [0, 4], [4, 2]]), np.ones(4, np.int32))
+    assert e.value.status == pic.PIC_ERR_MESH and "overlap" in pic.pic_last_error()
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mesh_create(nodes, tris, be, bt, walk_cap=4097)     # unbounded walks
+    assert e.value.status == pic.PIC_ERR_ARG
     m = pic.pic_mesh_create(nodes, tris, be, bt)
     with pytest.raises(pic.PicError) as e:
         pic.pic_sim_create(m, 0.01)                               # no SPAI yet
