@@ -85,6 +85,15 @@ __device__ __forceinline__ float self3(int k, float a, float b, float c) {
     return k == 0 ? a : (k == 1 ? b : c);
 }
 
+// The floating-point steps of the walk are spelled out with explicit rounding: the walk is
+// inlined at more than one call site, and a particle must get the same bits whichever site
+// (ring pass or final flush) handles it, so that runs are reproducible whatever order a
+// re-sort leaves the particles of one triangle in.
+// barycentric image of a meridian displacement: g_z d0 + g_rho d1
+__device__ __forceinline__ float bary_step(float gz, float gr, float d0, float d1) {
+    return __fmaf_rn(gz, d0, __fmul_rn(gr, d1));
+}
+
 struct Seg {
     int e0, e1, e2;  // end point (fixed point)
     int kx;          // exit edge, or -1 when the segment ends inside the triangle
@@ -121,8 +130,8 @@ __device__ __forceinline__ Seg segment_end(float f0, float f1, float f2, float d
     else if (sB <= sC) { r.kx = 1; r.sx = sB; }
     else { r.kx = 2; r.sx = sC; }
     const int kx = r.kx;
-    const float ci = fmaxf(self3(kx, f1, f2, f0) + r.sx * self3(kx, dl1, dl2, dl0), 0.f);
-    const float cj = fmaxf(self3(kx, f2, f0, f1) + r.sx * self3(kx, dl2, dl0, dl1), 0.f);
+    const float ci = fmaxf(__fmaf_rn(r.sx, self3(kx, dl1, dl2, dl0), self3(kx, f1, f2, f0)), 0.f);
+    const float cj = fmaxf(__fmaf_rn(r.sx, self3(kx, dl2, dl0, dl1), self3(kx, f2, f0, f1)), 0.f);
     int qi = f2fix(fminf(__fdividef(ci, ci + cj), 1.f));
     qi = min(max(qi, 0), LAM_ONE);
     const int qj = LAM_ONE - qi;
@@ -297,7 +306,7 @@ __device__ __forceinline__ void push_particle(const PushArgs<PF32> &a, int i, in
     __stcs(a.p.uz + i, uz);
 
     // end point in barycentric coordinates of t0
-    const float dl0 = G.x * d0 + G.y * d1, dl1 = G.z * d0 + G.w * d1;
+    const float dl0 = bary_step(G.x, G.y, d0, d1), dl1 = bary_step(G.z, G.w, d0, d1);
     const float le0 = f0 + dl0, le1 = f1 + dl1, le2 = f2 - (dl0 + dl1);
     crossed = !(le0 >= 0.f && le1 >= 0.f && le2 >= 0.f);
     // inside t0: round to fixed point summing to 2^22 (a rounding deficit of the remainder
@@ -405,13 +414,13 @@ __device__ __forceinline__ unsigned walk_pass(const PushArgs<PF32> &a, const QEn
         s1 = j == 1 ? 0 : (j == 2 ? ea : eb);
         s2 = j == 2 ? 0 : (j == 0 ? ea : eb);
         const float rest = 1.f - sg.sx;
-        d0 *= rest;
-        d1 *= rest;
+        d0 = __fmul_rn(d0, rest);
+        d1 = __fmul_rn(d1, rest);
         t = nb;
         const float4 G = __ldg(rec4(a.rec, t));
         EG = __ldg(rec4i(a.rec, t) + 5);
         NB = __ldg(rec4i(a.rec, t) + 6);
-        const float dl0 = G.x * d0 + G.y * d1, dl1 = G.z * d0 + G.w * d1;
+        const float dl0 = bary_step(G.x, G.y, d0, d1), dl1 = bary_step(G.z, G.w, d0, d1);
         sg = segment_end(fix2f(s0), fix2f(s1), fix2f(s2), dl0, dl1, -(dl0 + dl1), j);
         long long J0, J1, J2;
         currents(s0, s1, s2, sg, EG.w, J0, J1, J2);

@@ -82,3 +82,39 @@ def test_full_size_sampled_parity(pic):
     assert np.abs(g_u[live] - u[live]).max() < 1e-5 * np.abs(u).max()
     # the sample really exercised the walk
     assert np.count_nonzero(g_tri[live] != OP.locate(m, wl["z"][sample], wl["r"][sample])[0][live]) > 100
+
+
+def test_runs_are_bit_identical(pic):
+    """Two simulations from the same inputs end in the same state, bit for bit, after 40
+    steps (two re-sorts) on the BWO mesh with 2M particles: the fixed-point sums do not
+    depend on the order of the atomics, and a particle's walk does not depend on which
+    warp or ring pass handles it.  Compared per particle id (a re-sort may order the
+    particles of one triangle differently)."""
+    wl = bwo_workload(2_000_000)
+    mesh = pic.pic_mesh_create(wl["nodes"], wl["tris"], wl["be"], wl["bt"], eps0=EPS0, mu0=MU0,
+                               c=C0, precision=pic.PIC_FP32)
+    pic.pic_spai_build(mesh, 2, 1e-4)
+    info = pic.pic_mesh_info(mesh)
+    E0 = bwo_edge_field(info["n_edges"], wl["e_scale"], 7)
+    runs = []
+    for _ in range(2):
+        sim = pic.pic_sim_create(mesh, wl["dt"], wl["bz"], 2_000_000 + 1024)
+        pic.pic_sim_set_sort_interval(sim, 16)
+        pic.pic_fields_set(sim, E0, np.zeros(info["n_tris"]))
+        pic.pic_particles_inject(sim, wl["z"], wl["r"], wl["ur"], wl["up"], wl["uz"], QE, ME,
+                                 wl["weight"])
+        pic.pic_step(sim, 40)
+        d = pic.pic_diagnostics(sim, fields=True)
+        p = pic.pic_particles_get(sim)
+        order = np.argsort(p["pid"])
+        runs.append(({k: p[k][order] for k in ("tri", "lam", "u", "pid")}, d,
+                     pic.pic_charges_get(sim)))
+        pic.pic_sim_destroy(sim)
+    (p1, d1, q1), (p2, d2, q2) = runs
+    assert d1["n_crossings"] > 10_000_000
+    for k in ("tri", "lam", "u", "pid"):
+        assert np.array_equal(p1[k], p2[k]), k
+    for k in ("E", "B", "J", "n_crossings", "n_absorbed", "dce_nonzero"):
+        assert np.array_equal(d1[k], d2[k]), k
+    for a, b in zip(q1, q2):
+        assert np.array_equal(a, b)
