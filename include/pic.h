@@ -90,10 +90,12 @@ typedef struct {
                                 last step, in units of q_src/dt (Eq. DCE)                 */
     int64_t dce_nonzero;     /* FP32: nodes where the fixed-point DCE is not exactly 0  */
     double nr_dce_max;       /* max |NR_DCE| of Sec. 5.1.1 over nodes with net current   */
-    double dgl_drift;        /* max over non-PEC nodes of |res^n - res^ref|, res^n =
-                                D_div D^n - Q^n (Eq. DGL_RSD_REL), relative to max|Q|;
-                                res^ref is taken at the first step after the host last
-                                changed fields or particles                               */
+    double dgl_drift;        /* max over non-PEC nodes of |res^n - res^ref - Q_wall|,
+                                res^n = D_div D^n - Q^n (Eq. DGL_RSD_REL), relative to
+                                max|Q|; res^ref is taken at the first step after the host
+                                last changed fields or particles, and Q_wall is the charge
+                                removed at walls since then (it leaves Q without crossing
+                                an edge, so it shifts res by exactly that amount)         */
     double field_energy;     /* 1/2 E.star_eps.E + 1/2 B.star_mu^-1.B (per radian)        */
     double kinetic_energy;   /* sum (gamma-1) m c^2 w over live particles (3D)             */
     double q_absorbed;       /* charge removed at walls since creation (3D, q*w units)   */

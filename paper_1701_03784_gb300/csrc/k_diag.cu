@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) k_diag_nodes(DiagDev d, const typename P:
                                                     const typename P::Acc *Qn,
                                                     const typename P::Acc *Qp,
                                                     const typename P::Acc *Qabs,
-                                                    const typename P::Acc *Qpos, const double *D,
+                                                    const typename P::Acc *Qpos,
+                                                    const typename P::Acc *Qwall, const double *D,
                                                     double *dgl_ref, int set_ref, double q_scale,
                                                     double *out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -70,7 +71,12 @@ __global__ void __launch_bounds__(256) k_diag_nodes(DiagDev d, const typename P:
             double s = 0;
             for (int64_t q = d.node_ptr[k]; q < d.node_ptr[k + 1]; q++)
                 s += (double)d.node_sign[q] * D[d.node_edge[q]];
-            double res = s - qk;
+            // charge removed at walls since the reference leaves Q without crossing an
+            // edge: it shifts res by exactly that amount, which is taken out here
+            double qw;
+            if constexpr (P::fixed) qw = (double)(long long)Qwall[k] * LAM_INV * q_scale;
+            else qw = Qwall[k] * q_scale;
+            double res = s - qk - qw;
             if (set_ref) dgl_ref[k] = res;
             else dgl = fabs(res - dgl_ref[k]);
         }
@@ -127,11 +133,11 @@ __global__ void __launch_bounds__(256) k_diag_kinetic(Particles<P> p, const int6
 template <class P>
 void launch_diag(const DiagDev &d, const typename P::Acc *J, const typename P::Acc *Qn,
                  const typename P::Acc *Qp, const typename P::Acc *Qabs,
-                 const typename P::Acc *Qpos, const double *D,
+                 const typename P::Acc *Qpos, const typename P::Acc *Qwall, const double *D,
                  double *dgl_ref, int set_ref, const typename P::R *E, const typename P::R *B,
                  const typename P::R *mu_inv, Particles<P> p, const int64_t *n_slots,
                  int64_t n_bound, double q_scale, double inv_c2, double *out, cudaStream_t s) {
-    k_diag_nodes<P><<<(unsigned)((d.N0 + 255) / 256), 256, 0, s>>>(d, J, Qn, Qp, Qabs, Qpos, D, dgl_ref,
+    k_diag_nodes<P><<<(unsigned)((d.N0 + 255) / 256), 256, 0, s>>>(d, J, Qn, Qp, Qabs, Qpos, Qwall, D, dgl_ref,
                                                                    set_ref, q_scale, out);
     if (set_ref) return;
     int64_t ne = d.N1 > d.N2 ? d.N1 : d.N2;
@@ -188,7 +194,8 @@ void launch_acc_to_double(const typename P::Acc *a, double *out, int64_t n, doub
 
 #define PIC_INST(P)                                                                            \
     template void launch_diag<P>(const DiagDev &, const P::Acc *, const P::Acc *,              \
-                                 const P::Acc *, const P::Acc *, const P::Acc *, const double *, \
+                                 const P::Acc *, const P::Acc *, const P::Acc *, const P::Acc *, \
+                                 const double *,                                               \
                                  double *, int,                                                \
                                  const P::R *, const P::R *, const P::R *, Particles<P>,       \
                                  const int64_t *, int64_t, double, double, double *,           \

@@ -100,6 +100,16 @@ __global__ void __launch_bounds__(256) k_charge_from_current(FieldArgs<PF32> a) 
     if (div & (long long)(LAM_ONE - 1)) atomicAdd(a.counters + CNT_REMAINDER, 1ULL);
     long long qn = (long long)a.Qn[k] - (div >> LAM_BITS) - (long long)a.Qabs[k];
     a.Qnext[k] = (unsigned long long)qn;
+    a.Qwall[k] += a.Qabs[k];
+}
+
+// FP64 build, one thread per node: the charge removed at walls, summed since the
+// Gauss-law reference (the FP32 build does this in k_charge_from_current)
+template <class P>
+__global__ void __launch_bounds__(256) k_wall_charge(FieldArgs<P> a) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.N0) return;
+    a.Qwall[k] += a.Qabs[k];
 }
 
 template <class P>
@@ -111,6 +121,8 @@ template <class P>
 void launch_field_e(const FieldArgs<P> &a, cudaStream_t s) {
     if constexpr (P::fixed)
         k_charge_from_current<<<(unsigned)((a.N0 + 255) / 256), 256, 0, s>>>(a);
+    else
+        k_wall_charge<P><<<(unsigned)((a.N0 + 255) / 256), 256, 0, s>>>(a);
     k_field_r<P><<<(unsigned)((a.nf + 255) / 256), 256, 0, s>>>(a);
     int64_t rows = ((a.nf + 31) / 32) * 32;
     k_field_spmv<P><<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(a);

@@ -204,6 +204,7 @@ struct FieldArgs {
     const typename P::Acc *Qn;
     const typename P::Acc *Qabs;
     typename P::Acc *Qnext;
+    typename P::Acc *Qwall;     // N0: charge removed at walls since the Gauss-law reference
     unsigned long long *counters;
     int64_t N0;
 };
@@ -244,7 +245,8 @@ struct DiagDev {
 template <class P>
 void launch_diag(const DiagDev &d, const typename P::Acc *J, const typename P::Acc *Qn,
                  const typename P::Acc *Qp, const typename P::Acc *Qabs,
-                 const typename P::Acc *Qpos, const double *D, double *dgl_ref, int set_ref, const typename P::R *E,
+                 const typename P::Acc *Qpos, const typename P::Acc *Qwall, const double *D,
+                 double *dgl_ref, int set_ref, const typename P::R *E,
                  const typename P::R *B, const typename P::R *mu_inv, Particles<P> p,
                  const int64_t *n_slots, int64_t n_bound, double q_scale, double inv_c2,
                  double *out, cudaStream_t s);

@@ -96,6 +96,7 @@ struct SimImpl final : SimBase {
     int32_t *ell_col = nullptr;
     R *ell_val = nullptr;
     Acc *J = nullptr, *Qbuf[2] = {nullptr, nullptr}, *Qabs = nullptr, *qpos = nullptr;
+    Acc *Qwall = nullptr;   // charge removed at walls since the Gauss-law reference
     Particles<P> parts[2];
     int64_t *d_n = nullptr;
     unsigned long long *counters = nullptr;
@@ -225,7 +226,7 @@ struct SimImpl final : SimBase {
         // fields and accumulators
         if ((st = dalloc(E, mesh.N1)) || (st = dalloc(B, mesh.N2)) || (st = dalloc(D, mesh.N1)) ||
             (st = dalloc(r, nf)) || (st = dalloc(J, mesh.N1)) || (st = dalloc(Qbuf[0], mesh.N0)) ||
-            (st = dalloc(Qbuf[1], mesh.N0)) || (st = dalloc(Qabs, mesh.N0)) ||
+            (st = dalloc(Qbuf[1], mesh.N0)) || (st = dalloc(Qabs, mesh.N0)) || (st = dalloc(Qwall, mesh.N0)) ||
             (st = dalloc(qpos, mesh.N0)))
             return st;
         PIC_CUDA_TRY(cudaMemset(E, 0, sizeof(R) * mesh.N1));
@@ -312,6 +313,7 @@ struct SimImpl final : SimBase {
         a.Qn = nullptr;
         a.Qabs = Qabs;
         a.Qnext = nullptr;
+        a.Qwall = Qwall;
         a.counters = counters;
         a.N0 = m->N0;
         return a;
@@ -460,7 +462,8 @@ struct SimImpl final : SimBase {
         for (int64_t it = 0; it < n; it++) {
             if (dgl_dirty) {
                 // DGL reference res = D_div D^n - Q^n before the first step of this state
-                launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, D, dgl_ref, 1, E, B, mu_inv,
+                PIC_CUDA_TRY(cudaMemsetAsync(Qwall, 0, sizeof(Acc) * m->N0, s));
+                launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, Qwall, D, dgl_ref, 1, E, B, mu_inv,
                                parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
                 dgl_dirty = false;
             }
@@ -535,7 +538,8 @@ struct SimImpl final : SimBase {
 
     pic_status diagnostics(pic_diag *o, double *Eo, double *Bo, double *Jo, cudaStream_t s) override {
         if (dgl_dirty) {
-            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, D, dgl_ref, 1, E, B, mu_inv,
+            PIC_CUDA_TRY(cudaMemsetAsync(Qwall, 0, sizeof(Acc) * m->N0, s));
+            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, Qwall, D, dgl_ref, 1, E, B, mu_inv,
                            parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
             dgl_dirty = false;
         }
@@ -555,7 +559,7 @@ struct SimImpl final : SimBase {
                 qp = qpos;
             }
             // the last step wrote Q^{n+1} into Qn() and kept Q^n in the other buffer
-            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, qp, D, dgl_ref, 0, E, B, mu_inv,
+            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, qp, Qwall, D, dgl_ref, 0, E, B, mu_inv,
                            parts[cur], d_n, n_bound, q_scale(), inv_c2, diag_out, s);
             PIC_CUDA_TRY(cudaGetLastError());
             PIC_CUDA_TRY(cudaMemcpyAsync(out, diag_out, sizeof out, cudaMemcpyDeviceToHost, s));

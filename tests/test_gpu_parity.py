@@ -255,3 +255,31 @@ def test_raw_roundtrip(pic, cavity_oracle):
     after = pic.pic_particles_get(sim)
     for k in ("tri", "lam", "u"):
         assert np.array_equal(before[k], after[k])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_dgl_holds_with_charge_leaving_at_open_ends(pic, prec):
+    """Two-period BWO-shaped mesh with absorbing (non-conducting) ends, thermal particles
+    that leave through them: the charge removed there leaves Q without crossing an edge,
+    and once that is accounted for the Gauss-law residual D_div D - Q stays at round-off
+    (Eq. DGL_RSD_REL)."""
+    nodes, tris, be, bt = W.bwo_small_mesh(n_tri=3000, seed=4)
+    p = pic.PIC_FP64 if prec == "fp64" else pic.PIC_FP32
+    mesh = pic.pic_mesh_create(nodes, tris, be, bt, precision=p)
+    dt_max = pic.pic_spai_build(mesh)
+    info = pic.pic_mesh_info(mesh)
+    n = 20_000
+    sim = pic.pic_sim_create(mesh, 0.5 * dt_max, 0.1, n + 16)
+    pic.pic_sim_set_sort_interval(sim, 4)
+    pic.pic_fields_set(sim, W.random_edge_values(info["n_edges"], 1e-3, 50),
+                       np.zeros(info["n_tris"]))
+    z, r, ur, up, uz = W.uniform_in_mesh(nodes, tris, n, 51, sigma_u=0.8)
+    pic.pic_particles_inject(sim, z, r, ur, up, uz, -1.0, 1.0, 1e-3)
+    on_pec = Mesh(nodes, tris, be, bt).node_on_pec.astype(bool)
+    q_open = 0.0
+    for _ in range(60):
+        pic.pic_step(sim, 1)
+        q_open += np.abs(pic.pic_charges_get(sim)[2][~on_pec]).sum()
+    d = pic.pic_diagnostics(sim)
+    assert q_open > 0 and d["n_absorbed"] > 0        # charge left through the open ends
+    assert d["dgl_drift"] < (1e-10 if prec == "fp64" else 1e-5)
