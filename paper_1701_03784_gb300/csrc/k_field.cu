@@ -1,5 +1,7 @@
 // Field update of the mixed E-B leapfrog (Eqs. full_d_dfl, full_d_dal) and the per-step
 // triangle field records read by the particle kernel.
+#include <algorithm>
+
 #include "pic_internal.h"
 
 namespace pic {
@@ -7,10 +9,17 @@ namespace pic {
 // K3, one thread per face: B^{n+1/2} = B^{n-1/2} - dt (D_curl E^n)_f, and the record's
 // field coefficients: E(lambda) = sum_k E_k (lambda_a grad lambda_b - lambda_b grad
 // lambda_a) = sum_m lambda_m c_m, and B_phi = (B^{n+1/2} + B^{n-1/2}) / (2A) (W2 = 1/A).
+// The same launch clears the step's accumulators (J per edge, Q_abs per node, and in the
+// FP64 build Q^{n+1}, which the particle kernel accumulates).
 template <class P>
 __global__ void __launch_bounds__(256) k_field_b(FieldArgs<P> a) {
     using R = typename P::R;
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < a.N1) a.J[f] = 0;
+    if (f < a.N0) {
+        a.Qabs[f] = 0;
+        if constexpr (!P::fixed) a.Qnext[f] = 0;
+    }
     if (f >= a.N2) return;
     TriRec<R> &rc = a.rec[f];
     const int32_t flags = rc.flags;
@@ -40,12 +49,32 @@ __global__ void __launch_bounds__(256) k_field_b(FieldArgs<P> a) {
     }
 }
 
+// Per node, after the particle step.  FP32 build: Q^{n+1} = Q^n - (D_div J)/2^22 -
+// Q_absorbed.  Per particle, the segment currents at a node sum to 2^22 (lambda^start -
+// lambda^end) in the fixed-point units (the identity behind Eq. DCE), so D_div J is
+// divisible by 2^22 and the result equals Eq. charge evaluated at the new positions
+// exactly; a non-zero remainder would be a broken invariant and is counted.  Both builds:
+// the charge removed at walls is summed since the Gauss-law reference.
+template <class P>
+__device__ __forceinline__ void node_update(const FieldArgs<P> &a, int64_t k) {
+    if constexpr (P::fixed) {
+        long long div = 0;
+        for (int64_t q = a.node_ptr[k]; q < a.node_ptr[k + 1]; q++)
+            div += (long long)a.node_sign[q] * (long long)a.J[a.node_edge[q]];
+        if (div & (long long)(LAM_ONE - 1)) atomicAdd(a.counters + CNT_REMAINDER, 1ULL);
+        long long qn = (long long)a.Qn[k] - (div >> LAM_BITS) - (long long)a.Qabs[k];
+        a.Qnext[k] = (unsigned long long)qn;
+    }
+    a.Qwall[k] += a.Qabs[k];
+}
+
 // K4a, one thread per free edge: r = D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}; the DGL
-// auxiliary flux D += dt r.
+// auxiliary flux D += dt r.  The same launch does the per-node update (thread k, node k).
 template <class P>
 __global__ void __launch_bounds__(256) k_field_r(FieldArgs<P> a) {
     using R = typename P::R;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.N0) node_update<P>(a, i);
     if (i >= a.nf) return;
     int32_t e = a.free_edges[i];
     double r = 0;
@@ -86,44 +115,16 @@ __global__ void __launch_bounds__(256) k_field_spmv(FieldArgs<P> a) {
     if (row < a.nf) a.E[a.free_edges[row]] += a.dt * acc;
 }
 
-// FP32 build, one thread per node: Q^{n+1} = Q^n - (D_div J)/2^22 - Q_absorbed.  Per
-// particle, the segment currents at a node sum to 2^22 (lambda^start - lambda^end) in the
-// fixed-point units (the identity behind Eq. DCE), so D_div J is divisible by 2^22 and the
-// result equals Eq. charge evaluated at the new positions exactly.  A non-zero remainder
-// would be a broken invariant; it is counted.
-__global__ void __launch_bounds__(256) k_charge_from_current(FieldArgs<PF32> a) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.N0) return;
-    long long div = 0;
-    for (int64_t q = a.node_ptr[k]; q < a.node_ptr[k + 1]; q++)
-        div += (long long)a.node_sign[q] * (long long)a.J[a.node_edge[q]];
-    if (div & (long long)(LAM_ONE - 1)) atomicAdd(a.counters + CNT_REMAINDER, 1ULL);
-    long long qn = (long long)a.Qn[k] - (div >> LAM_BITS) - (long long)a.Qabs[k];
-    a.Qnext[k] = (unsigned long long)qn;
-    a.Qwall[k] += a.Qabs[k];
-}
-
-// FP64 build, one thread per node: the charge removed at walls, summed since the
-// Gauss-law reference (the FP32 build does this in k_charge_from_current)
-template <class P>
-__global__ void __launch_bounds__(256) k_wall_charge(FieldArgs<P> a) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.N0) return;
-    a.Qwall[k] += a.Qabs[k];
-}
-
 template <class P>
 void launch_field_b(const FieldArgs<P> &a, cudaStream_t s) {
-    k_field_b<P><<<(unsigned)((a.N2 + 255) / 256), 256, 0, s>>>(a);
+    const int64_t n = std::max(a.N2, std::max(a.N1, a.N0));
+    k_field_b<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
 }
 
 template <class P>
 void launch_field_e(const FieldArgs<P> &a, cudaStream_t s) {
-    if constexpr (P::fixed)
-        k_charge_from_current<<<(unsigned)((a.N0 + 255) / 256), 256, 0, s>>>(a);
-    else
-        k_wall_charge<P><<<(unsigned)((a.N0 + 255) / 256), 256, 0, s>>>(a);
-    k_field_r<P><<<(unsigned)((a.nf + 255) / 256), 256, 0, s>>>(a);
+    const int64_t n = std::max(a.nf, a.N0);
+    k_field_r<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
     int64_t rows = ((a.nf + 31) / 32) * 32;
     k_field_spmv<P><<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(a);
 }

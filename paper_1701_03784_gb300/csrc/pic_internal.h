@@ -187,7 +187,7 @@ struct FieldArgs {
     const typename P::R *mu_inv;// N2
     const int32_t *edge_face;   // N1 x 2: (face+1) * sign, 0 if none
     const int32_t *free_edges;  // nf
-    const typename P::Acc *J;   // N1
+    typename P::Acc *J;         // N1 (zeroed by the face kernel before the particle step)
     double *D;                  // N1 auxiliary dual flux (DGL)
     typename P::R *r;           // nf scratch: D_curl^T star_mu^-1 B - J
     // M in sliced ELL: slices of 32 rows, column-major inside a slice
@@ -202,7 +202,7 @@ struct FieldArgs {
     const int32_t *node_edge;
     const int8_t *node_sign;    // +1 tail, -1 head
     const typename P::Acc *Qn;
-    const typename P::Acc *Qabs;
+    typename P::Acc *Qabs;      // N0 (zeroed by the face kernel before the particle step)
     typename P::Acc *Qnext;
     typename P::Acc *Qwall;     // N0: charge removed at walls since the Gauss-law reference
     unsigned long long *counters;

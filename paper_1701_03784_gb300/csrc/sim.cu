@@ -468,10 +468,8 @@ struct SimImpl final : SimBase {
                 dgl_dirty = false;
             }
             Acc *Qnext = Qbuf[1 - qcur];
-            PIC_CUDA_TRY(cudaMemsetAsync(J, 0, sizeof(Acc) * m->N1, s));
-            // FP32: Q^{n+1} is written whole by the per-node charge kernel
-            if constexpr (!P::fixed) PIC_CUDA_TRY(cudaMemsetAsync(Qnext, 0, sizeof(Acc) * m->N0, s));
-            PIC_CUDA_TRY(cudaMemsetAsync(Qabs, 0, sizeof(Acc) * m->N0, s));
+            // the face kernel clears J, Q_abs and (FP64) Q^{n+1}; in the FP32 build Q^{n+1} is
+            // written whole by the per-node update
             fa.Qn = Qn();
             fa.Qnext = Qnext;
             launch_field_b<P>(fa, s);
