@@ -109,7 +109,7 @@ def push_traffic():
             if ":" in line:
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("k_push.cu sha256[:16]") == h:
+        if vals.get("k_push_f32.cu sha256[:16]") == h:
             return float(vals["dram bytes per launch (full size)"])
     except (OSError, KeyError, ValueError):
         pass
