@@ -278,8 +278,8 @@ def main():
                   if args.sort_interval and k % args.sort_interval == 0)
     launches = 4 * args.steps + 5 * resorts
 
-    # end to end through the C ABI with host buffers: upload the state from pinned
-    # memory, step, read it back, every step
+    # end to end through the C ABI with host buffers: every step uploads the state from
+    # pinned memory, steps and reads it back (pic_step_host)
     n_slots = pic.pic_particles_count(sim)
     bpp = pic.pic_particles_raw_bytes(sim)
     host = torch.empty(n_slots * bpp, dtype=torch.uint8, pin_memory=True)
@@ -288,10 +288,7 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.e2e_steps):
-        pic.pic_particles_raw_set(sim, host.data_ptr(), n_slots)
-        pic.pic_step(sim, 1)
-        pic.pic_particles_raw_get(sim, host.data_ptr(), n_slots)
+    pic.pic_step_host(sim, host.data_ptr(), n_slots, args.e2e_steps)
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)

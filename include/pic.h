@@ -229,6 +229,17 @@ pic_status pic_particles_raw_get(pic_sim *s, void *host_dst, int64_t n_slots,
 pic_status pic_particles_raw_set(pic_sim *s, const void *host_src, int64_t n_slots,
                                  void *cuda_stream);
 
+/* n_steps steps of Sec. 3's cycle for a particle state that lives in page-locked host
+ * memory between steps (raw layout above, n_slots slots, n_slots at most the capacity):
+ * every step uploads it, steps, and writes it back.  Slots beyond the live count after a
+ * re-sort removed particles are unspecified on return.  The download of one step runs on
+ * an internal stream and overlaps, chunk by chunk, the upload of the next; the call is
+ * asynchronous on cuda_stream, which waits for the last download.  Errors: PIC_ERR_ARG
+ * (null state, bad counts), PIC_ERR_CUDA.  The host buffer must stay untouched until the
+ * stream reaches that point. */
+pic_status pic_step_host(pic_sim *s, void *host_state, int64_t n_slots, int64_t n_steps,
+                         void *cuda_stream);
+
 /* Device time of the particle kernel over the steps enqueued since the last call
  * (CUDA events around each launch on the step's stream); synchronous.  Writes the
  * total milliseconds and the number of launches. */

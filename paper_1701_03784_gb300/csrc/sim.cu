@@ -66,6 +66,7 @@ struct SimBase {
     virtual int64_t raw_bytes() const = 0;
     virtual pic_status raw_get(void *dst, int64_t n, cudaStream_t s) = 0;
     virtual pic_status raw_set(const void *src, int64_t n, cudaStream_t s) = 0;
+    virtual pic_status step_host(void *state, int64_t n, int64_t steps, cudaStream_t s) = 0;
     virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
     virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
     int32_t sort_interval = 16;
@@ -105,12 +106,22 @@ struct SimImpl final : SimBase {
     double *dgl_ref = nullptr, *diag_out = nullptr;
 
     bool timing_on = false;
+    // host round trips (step_host): downloads run on their own stream, chunk by chunk
+    static constexpr int RT_CHUNKS = 8;
+    cudaStream_t rt_stream = nullptr;
+    cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
 
     ~SimImpl() override {
         cudaSetDevice(device);
         cudaDeviceSynchronize();
+        if (rt_stream) {
+            for (auto e : rt_chunk) cudaEventDestroy(e);
+            cudaEventDestroy(rt_step);
+            cudaEventDestroy(rt_done);
+            cudaStreamDestroy(rt_stream);
+        }
         for (auto &e : ev_pending) {
             cudaEventDestroy(e.first);
             cudaEventDestroy(e.second);
@@ -754,6 +765,65 @@ struct SimImpl final : SimBase {
         dgl_dirty = true;
         return PIC_OK;
     }
+
+    // slots [c0, c1) of the raw state, host <-> device (one copy per array)
+    pic_status copy_slots(char *h, int64_t n, int64_t c0, int64_t c1, bool up, cudaStream_t s) {
+        const Particles<P> &p = parts[cur];
+        void *dev[6] = {p.tri, p.l0, p.l1, p.ur, p.up, p.uz};
+        const size_t sz[6] = {4, sizeof(Lam), sizeof(Lam), sizeof(R), sizeof(R), sizeof(R)};
+        for (int k = 0; k < 6; k++) {
+            char *d = static_cast<char *>(dev[k]) + sz[k] * c0;
+            char *hk = h + sz[k] * c0;
+            const size_t bytes = sz[k] * (size_t)(c1 - c0);
+            if (up) PIC_CUDA_TRY(cudaMemcpyAsync(d, hk, bytes, cudaMemcpyHostToDevice, s));
+            else PIC_CUDA_TRY(cudaMemcpyAsync(hk, d, bytes, cudaMemcpyDeviceToHost, s));
+            h += sz[k] * n;
+        }
+        return PIC_OK;
+    }
+
+    pic_status step_host(void *state, int64_t n, int64_t steps, cudaStream_t s) override {
+        if (!state || n < 0 || n > cap || steps < 0) {
+            set_error("pic_step_host: bad argument");
+            return PIC_ERR_ARG;
+        }
+        if (!rt_stream) {
+            PIC_CUDA_TRY(cudaStreamCreateWithFlags(&rt_stream, cudaStreamNonBlocking));
+            for (auto &e : rt_chunk) PIC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_step, cudaEventDisableTiming));
+            PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_done, cudaEventDisableTiming));
+        }
+        char *h = static_cast<char *>(state);
+        const int64_t chunk = (n + RT_CHUNKS - 1) / RT_CHUNKS;
+        pic_status st;
+        for (int64_t k = 0; k < steps; k++) {
+            // upload; chunk c waits only for the previous step's download of chunk c, so the
+            // two copy directions overlap
+            for (int c = 0; c < RT_CHUNKS; c++) {
+                const int64_t c0 = std::min(n, c * chunk), c1 = std::min(n, c0 + chunk);
+                if (k > 0) PIC_CUDA_TRY(cudaStreamWaitEvent(s, rt_chunk[c], 0));
+                if (c1 > c0 && (st = copy_slots(h, n, c0, c1, true, s)) != PIC_OK) return st;
+            }
+            if (k == 0) {
+                // the caller's state: its slot count, and a new Gauss-law reference
+                PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+                n_bound = n;
+                dgl_dirty = true;
+            }
+            if ((st = step(1, s)) != PIC_OK) return st;
+            PIC_CUDA_TRY(cudaEventRecord(rt_step, s));
+            PIC_CUDA_TRY(cudaStreamWaitEvent(rt_stream, rt_step, 0));
+            for (int c = 0; c < RT_CHUNKS; c++) {
+                const int64_t c0 = std::min(n, c * chunk), c1 = std::min(n, c0 + chunk);
+                if (c1 > c0 && (st = copy_slots(h, n, c0, c1, false, rt_stream)) != PIC_OK)
+                    return st;
+                PIC_CUDA_TRY(cudaEventRecord(rt_chunk[c], rt_stream));
+            }
+        }
+        PIC_CUDA_TRY(cudaEventRecord(rt_done, rt_stream));
+        PIC_CUDA_TRY(cudaStreamWaitEvent(s, rt_done, 0));
+        return PIC_OK;
+    }
 };
 
 }  // namespace pic
@@ -908,6 +978,12 @@ extern "C" pic_status pic_particles_raw_get(pic_sim *s, void *dst, int64_t n, vo
 extern "C" pic_status pic_particles_raw_set(pic_sim *s, const void *src, int64_t n, void *st) {
     SIM_CHECK(s, "pic_particles_raw_set");
     return s->impl->raw_set(src, n, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_step_host(pic_sim *s, void *state, int64_t n_slots, int64_t n_steps,
+                                     void *st) {
+    SIM_CHECK(s, "pic_step_host");
+    return s->impl->step_host(state, n_slots, n_steps, (cudaStream_t)st);
 }
 
 extern "C" pic_status pic_kernel_timing(pic_sim *s, int32_t enable, double *ms, int64_t *launches,

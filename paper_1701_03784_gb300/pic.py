@@ -73,6 +73,7 @@ _SIGS = {
     "pic_particles_raw_bytes": [_P, _P],
     "pic_particles_raw_get": [_P, _P, _I64, _P],
     "pic_particles_raw_set": [_P, _P, _I64, _P],
+    "pic_step_host": [_P, _P, _I64, _I64, _P],
     "pic_kernel_timing": [_P, _I32, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
@@ -346,6 +347,13 @@ def pic_particles_raw_get(sim, host_ptr, n_slots, stream=None):
 def pic_particles_raw_set(sim, host_ptr, n_slots, stream=None):
     _check(_lib.pic_particles_raw_set(sim.ptr, ctypes.c_void_p(host_ptr), int(n_slots),
                                       _stream(stream)), "pic_particles_raw_set")
+
+
+def pic_step_host(sim, host_ptr, n_slots, n_steps=1, stream=None):
+    """n_steps steps with the raw state in the page-locked host buffer at host_ptr
+    (n_slots * raw_bytes bytes): uploaded, stepped and written back every step."""
+    _check(_lib.pic_step_host(sim.ptr, ctypes.c_void_p(host_ptr), int(n_slots), int(n_steps),
+                              _stream(stream)), "pic_step_host")
 
 
 def pic_kernel_timing(sim, enable=True, stream=None):
