@@ -106,8 +106,8 @@ def push_traffic():
         h = hashlib.sha256(src).hexdigest()[:16]
         vals = {}
         for line in open(PUSH_PROFILE):
-            if ":" in line:
-                k, v = line.split(":", 1)
+            if ": " in line:
+                k, v = line.split(": ", 1)
                 vals[k.strip()] = v.strip()
         if vals.get("k_push_f32.cu sha256[:16]") == h:
             return float(vals["dram bytes per launch (full size)"])
@@ -139,26 +139,31 @@ class OracleSample:
         self.J, self.Q, self.Qa = np.zeros(m.N1), np.zeros(m.N0), np.zeros(m.N0)
         self.wl = wl
         self.n = n_sample
+        self.n_edges = m.N1
         self.q_src = wl["weight"] * QE / (2 * math.pi)
 
     def step(self):
-        """One particle step of the sample; returns its wall time in seconds."""
+        """One particle step of the sample; returns (wall time in seconds, particles
+        pushed: the live ones at the start of the step)."""
+        live = int(np.count_nonzero(self.tri >= 0))
         t0 = time.perf_counter()
         self.J[:] = 0
         self.Q[:] = 0
         self.OP.push(self.pm, self.E, self.Bavg, self.wl["bz"], self.wl["dt"], QE / ME, C0,
                      self.q_src, self.tri, self.lam, self.u, self.J, self.Q, self.Qa)
-        return time.perf_counter() - t0
+        return time.perf_counter() - t0, live
 
 
 def cpu_baseline(wl, budget_s=15.0):
     s = OracleSample(wl)
-    done, el = 0, 0.0
+    done, el, pushed = 0, 0.0, 0
     while el < budget_s:
-        el += s.step()
+        dt_s, n = s.step()
+        el += dt_s
+        pushed += n
         done += 1
     live = int(np.count_nonzero(s.tri >= 0))
-    return {"value": s.n * done / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+    return {"value": pushed / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": "%d of %d beam particles, %d steps, same mesh, fields and dt; FP64 C "
                       "oracle particle loop (gather, Boris, walk, scatter), single thread; %d "
                       "live at end" % (s.n, len(wl["z"]), done, live)}
@@ -176,6 +181,16 @@ def reduce_over_ranks(ms, e2e_ms, n_particles, n_slots, dist=None, device="cpu")
     return t.tolist(), c.tolist()
 
 
+def run_config(args, n_tris, n_edges, dt):
+    """The workload named in both arms' JSON lines."""
+    return {"workload": "single BWO (rippled SWS, 12 periods), %d triangles, %d particles, "
+                        "FP32 + int64 fixed-point J/Q" % (n_tris, args.particles),
+            "n_tris": n_tris, "n_edges": n_edges, "particles": args.particles, "dt_s": dt,
+            "sort_interval": args.sort_interval,
+            "l2": "inputs larger than L2 (particle state %d MB)" % (args.particles * 24 // 2 ** 20),
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -183,13 +198,13 @@ def run_reference(args):
     wl = workload(args.particles)
     wl["dt"] = args.dt or DT_BWO
     s = OracleSample(wl)
-    per_step = []
+    t, pushed = 0.0, 0
     for i in range(args.warmup + args.steps):
-        el = s.step()
+        el, n = s.step()
         if i >= args.warmup:
-            per_step.append(el)
-    t = sum(per_step)
-    value = CPU_SAMPLE * args.steps / t
+            t += el
+            pushed += n
+    value = pushed / t
     cb = {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
           "sample": "%d of %d particles per step (bounded sample of the workload), FP64 C "
                     "oracle particle loop, single thread" % (CPU_SAMPLE, args.particles)}
@@ -197,8 +212,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "single BWO, ~200k triangles, %d particles (CPU sample %d)"
-                                   % (args.particles, CPU_SAMPLE)},
+            "config": run_config(args, len(wl["tris"]), s.n_edges, wl["dt"]),
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -308,15 +322,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "single BWO (rippled SWS, 12 periods), %d triangles, %d "
-                                   "particles, FP32 + int64 fixed-point J/Q" % (info["n_tris"],
-                                                                              args.particles),
-                       "n_tris": info["n_tris"], "n_edges": info["n_edges"],
-                       "particles": args.particles, "dt_s": dt, "dt_over_stable": dt / dt_max,
-                       "sort_interval": args.sort_interval,
-                       "l2": "inputs larger than L2 (particle state %d MB)"
-                             % (args.particles * 24 // 2 ** 20),
-                       "parallelism": "replicas" if args.gpus > 1 else "single"},
+            "config": run_config(args, info["n_tris"], info["n_edges"], dt),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_push_f32", "peak_kind": peak_kind,
@@ -327,7 +333,8 @@ def main():
                     "steps": args.e2e_steps},
             "gpu_launches": launches,
             "clocks": clocks,
-            "checks": {"dce_nonzero_nodes": diag["dce_nonzero"], "dgl_drift": diag["dgl_drift"],
+            "checks": {"dt_over_stable": dt / dt_max,
+                       "dce_nonzero_nodes": diag["dce_nonzero"], "dgl_drift": diag["dgl_drift"],
                        "walk_overflows": diag["walk_overflows"], "live_particles": n_end,
                        "absorbed": diag["n_absorbed"]},
         }
