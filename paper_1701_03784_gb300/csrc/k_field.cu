@@ -21,6 +21,38 @@ __global__ void __launch_bounds__(256) k_field_b(FieldArgs<P> a) {
         if constexpr (!P::fixed) a.Qnext[f] = 0;
     }
     if (f >= a.N2) return;
+    if constexpr (sizeof(R) == 4) {
+        // FP32 record: 16-byte groups (g | rho, 1/A | c0 c1 | c2, B_phi, pad | nodes, flags |
+        // edges, flags), read and written as vectors
+        float4 *R4 = reinterpret_cast<float4 *>(a.rec + f);
+        const float4 G = R4[0], RH = R4[1];
+        const int4 EG = reinterpret_cast<const int4 *>(a.rec + f)[5];
+        const float g[3][2] = {{G.x, G.y}, {G.z, G.w}, {-G.x - G.z, -G.y - G.w}};
+        float c[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        float curl = 0;
+        const int ek[3] = {EG.x, EG.y, EG.z};
+        float E3[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) E3[k] = a.E[ek[k]];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float Ek = E3[k];
+            const int i = (k + 1) % 3, j = (k + 2) % 3;
+            const bool fwd = (EG.w >> k) & 1;
+            const int ta = fwd ? i : j, hb = fwd ? j : i;
+            c[ta][0] += Ek * g[hb][0];
+            c[ta][1] += Ek * g[hb][1];
+            c[hb][0] -= Ek * g[ta][0];
+            c[hb][1] -= Ek * g[ta][1];
+            curl += fwd ? Ek : -Ek;
+        }
+        const float Bold = a.B[f];
+        const float Bnew = Bold - a.dt * curl;
+        a.B[f] = Bnew;
+        R4[2] = make_float4(c[0][0], c[0][1], c[1][0], c[1][1]);
+        R4[3] = make_float4(c[2][0], c[2][1], 0.5f * (Bnew + Bold) * RH.w, 0.f);
+        return;
+    }
     TriRec<R> &rc = a.rec[f];
     const int32_t flags = rc.flags;
     R g[3][2] = {{rc.g[0], rc.g[1]}, {rc.g[2], rc.g[3]}, {-rc.g[0] - rc.g[2], -rc.g[1] - rc.g[3]}};
@@ -76,11 +108,12 @@ __global__ void __launch_bounds__(256) k_field_r(FieldArgs<P> a) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.N0) node_update<P>(a, i);
     if (i >= a.nf) return;
-    int32_t e = a.free_edges[i];
+    const int32_t e = a.free_edges[i];
+    const int2 ef = reinterpret_cast<const int2 *>(a.edge_face)[i];
     double r = 0;
 #pragma unroll
     for (int q = 0; q < 2; q++) {
-        int32_t fs = a.edge_face[2 * e + q];
+        int32_t fs = q == 0 ? ef.x : ef.y;
         if (fs == 0) continue;
         int32_t f = (fs > 0 ? fs : -fs) - 1;
         double hf = (double)a.mu_inv[f] * (double)a.B[f];

@@ -185,7 +185,7 @@ struct FieldArgs {
     typename P::R *E;           // N1
     typename P::R *B;           // N2, B^{n-1/2} in, B^{n+1/2} out
     const typename P::R *mu_inv;// N2
-    const int32_t *edge_face;   // N1 x 2: (face+1) * sign, 0 if none
+    const int32_t *edge_face;   // nf x 2, per free edge: (face+1) * sign, 0 if none
     const int32_t *free_edges;  // nf
     typename P::Acc *J;         // N1 (zeroed by the face kernel before the particle step)
     double *D;                  // N1 auxiliary dual flux (DGL)

@@ -205,12 +205,15 @@ struct SimImpl final : SimBase {
         if ((st = upload(rec, hr)) != PIC_OK) return st;
         std::vector<R> hmu(mesh.mu_inv.begin(), mesh.mu_inv.end());
         if ((st = upload(mu_inv, hmu)) != PIC_OK) return st;
-        std::vector<int32_t> hef(2 * mesh.N1, 0);
-        for (int64_t e = 0; e < mesh.N1; e++)
+        // the two faces of each free edge, in free-edge order
+        std::vector<int32_t> hef(2 * std::max<int64_t>(nf, 1), 0);
+        for (int64_t i = 0; i < nf; i++) {
+            const int64_t e = mesh.free_edges[i];
             for (int q2 = 0; q2 < 2; q2++) {
                 int32_t f = mesh.edge_face[2 * e + q2];
-                if (f >= 0) hef[2 * e + q2] = (f + 1) * mesh.edge_face_sign[2 * e + q2];
+                if (f >= 0) hef[2 * i + q2] = (f + 1) * mesh.edge_face_sign[2 * e + q2];
             }
+        }
         if ((st = upload(edge_face, hef)) != PIC_OK) return st;
         if ((st = upload(free_edges, mesh.free_edges)) != PIC_OK) return st;
         // M as sliced ELL (slices of 32 rows, column-major inside a slice)
