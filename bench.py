@@ -220,6 +220,82 @@ def run_reference(args):
     return 0
 
 
+SWEEP_RUN_STEPS = 100_000   # one run of an instance: the single-BWO configuration's length
+
+
+def run_sweep(args):
+    """Batched ripple sweep: the union of N seeded BWO instances advanced as one
+    simulation (one particle-kernel launch per step over every instance) against the same
+    N instances run one after another, each as its own simulation, over the same steps and
+    time step.  Runs per hour are for runs of SWEEP_RUN_STEPS steps."""
+    import torch
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import pic
+    from workloads.sweep import sweep_instance, union, WEIGHT
+    from workloads.bwo import BZ_BWO
+    t_setup = time.time()
+    ins = [sweep_instance(i) for i in range(args.sweep)]
+    u = union(ins)
+
+    def make(x):
+        mesh = pic.pic_mesh_create(x["nodes"], x["tris"], x["be"], x["bt"], eps0=EPS0, mu0=MU0,
+                                   c=C0, precision=pic.PIC_FP32)
+        return mesh, pic.pic_spai_build(mesh, 2, 1e-4)
+
+    mesh_u, dt_u = make(u)
+    dt = 0.5 * dt_u
+    stream = torch.cuda.current_stream()
+
+    def timed(mesh, x):
+        info = pic.pic_mesh_info(mesh)
+        sim = pic.pic_sim_create(mesh, dt, BZ_BWO, len(x["z"]) + 1024)
+        pic.pic_sim_set_sort_interval(sim, args.sort_interval)
+        pic.pic_fields_set(sim, np.zeros(info["n_edges"]), np.zeros(info["n_tris"]))
+        pic.pic_particles_inject(sim, x["z"], x["r"], x["ur"], x["up"], x["uz"], QE, ME, WEIGHT)
+        pic.pic_step(sim, args.sweep_warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pic.pic_step(sim, args.sweep_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d = pic.pic_diagnostics(sim)
+        pic.pic_sim_destroy(sim)
+        return e0.elapsed_time(e1), d
+
+    setup_s = time.time() - t_setup
+    ms_b, d_b = timed(mesh_u, u)
+    ms_p = 0.0
+    for x in ins:
+        mesh, _ = make(x)
+        ms, _ = timed(mesh, x)
+        ms_p += ms
+        del mesh
+    k = args.sweep_steps
+    step_b, step_p = ms_b / k, ms_p / k
+    n_part = len(u["z"])
+    runs_b = args.sweep * 3600.0 / (SWEEP_RUN_STEPS * step_b * 1e-3)
+    runs_p = args.sweep * 3600.0 / (SWEEP_RUN_STEPS * step_p * 1e-3)
+    print(json.dumps({
+        "metric": "batched runs/h vs plain", "value": runs_b, "unit": "runs/h",
+        "higher_is_better": True, "plain": runs_p, "speedup": runs_b / runs_p,
+        "n_gpus": 1, "steps": k, "warmup": args.sweep_warmup, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched ripple sweep, %d BWO instances (seeds 0..%d)"
+                               % (args.sweep, args.sweep - 1),
+                   "instances": args.sweep, "triangles": int(len(u["tris"])),
+                   "particles": int(n_part), "dt_s": dt, "sort_interval": args.sort_interval,
+                   "run_steps": SWEEP_RUN_STEPS},
+        "ms_per_step": {"batched": step_b, "plain_sum": step_p},
+        "particle_steps_per_s": {"batched": n_part / (step_b * 1e-3),
+                                 "plain": n_part / (step_p * 1e-3)},
+        "checks": {"dce_nonzero_nodes": d_b["dce_nonzero"], "walk_overflows": d_b["walk_overflows"],
+                   "live_particles": d_b["n_particles"]},
+        "setup_s": setup_s}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,9 +307,15 @@ def main():
     ap.add_argument("--dt", type=float, default=None)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", type=int, default=0,
+                    help="batched ripple sweep over this many instances instead")
+    ap.add_argument("--sweep-steps", type=int, default=64)
+    ap.add_argument("--sweep-warmup", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

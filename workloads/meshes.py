@@ -37,9 +37,11 @@ def _segment_points(a, b, h):
 
 
 def jittered_delaunay(z0, z1, R, n_tri, seed, jitter=0.2,
-                      end_tags=(BC_PEC, BC_PEC), wall_tag=BC_PEC, breaks=()):
+                      end_tags=(BC_PEC, BC_PEC), wall_tag=BC_PEC, breaks=(), wall_refine=1.0):
     """Mesh of {z0<=z<=z1, 0<=rho<=R(z)} with about ``n_tri`` triangles.
 
+    ``wall_refine`` < 1 places the wall points closer than the interior spacing (for
+    walls whose curvature a coarse mesh does not resolve).
     Returns (nodes, tris, bedges, btags); see the package docstring for layouts.
     """
     rng = np.random.default_rng(seed)
@@ -58,7 +60,7 @@ def jittered_delaunay(z0, z1, R, n_tri, seed, jitter=0.2,
         re = _segment_points(0.0, float(R(np.array([ze]))[0]), h)[1:]
         pts.append(np.stack([np.full_like(re, ze), re], 1))
     # wall (corners excluded: they belong to the end planes)
-    zw, rw = _wall_points(R, z0, z1, h, breaks)
+    zw, rw = _wall_points(R, z0, z1, h * wall_refine, breaks)
     pts.append(np.stack([zw[1:-1], rw[1:-1]], 1))
     n_boundary = sum(len(p) for p in pts)
 
@@ -170,11 +172,12 @@ def bwo_wall(r0=1.5e-2, ripple=0.4e-2, period=1.67e-2, n_periods=12, guide=3e-2)
     return R, z_end, (zs0, zs1)
 
 
-def bwo_mesh(n_tri=200_000, seed=1002, **wall):
+def bwo_mesh(n_tri=200_000, seed=1002, wall_refine=1.0, **wall):
     """Single backward-wave oscillator: rippled wall, 12 periods, guides, SI metres."""
     R, z_end, sws = bwo_wall(**wall)
     return jittered_delaunay(0.0, z_end, R, n_tri, seed,
-                             end_tags=(BC_ABSORB, BC_ABSORB), wall_tag=BC_PEC, breaks=sws)
+                             end_tags=(BC_ABSORB, BC_ABSORB), wall_tag=BC_PEC, breaks=sws,
+                             wall_refine=wall_refine)
 
 
 def bwo_small_mesh(n_tri=3000, seed=1012):
