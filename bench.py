@@ -251,6 +251,7 @@ def run_sweep(args):
         info = pic.pic_mesh_info(mesh)
         sim = pic.pic_sim_create(mesh, dt, BZ_BWO, len(x["z"]) + 1024)
         pic.pic_sim_set_sort_interval(sim, args.sort_interval)
+        pic.pic_sim_set_graph(sim, not args.no_graph)
         pic.pic_fields_set(sim, np.zeros(info["n_edges"]), np.zeros(info["n_tris"]))
         pic.pic_particles_inject(sim, x["z"], x["r"], x["ur"], x["up"], x["uz"], QE, ME, WEIGHT)
         pic.pic_step(sim, args.sweep_warmup)
@@ -286,7 +287,7 @@ def run_sweep(args):
                                % (args.sweep, args.sweep - 1),
                    "instances": args.sweep, "triangles": int(len(u["tris"])),
                    "particles": int(n_part), "dt_s": dt, "sort_interval": args.sort_interval,
-                   "run_steps": SWEEP_RUN_STEPS},
+                   "run_steps": SWEEP_RUN_STEPS, "cuda_graph": not args.no_graph},
         "ms_per_step": {"batched": step_b, "plain_sum": step_p},
         "particle_steps_per_s": {"batched": n_part / (step_b * 1e-3),
                                  "plain": n_part / (step_p * 1e-3)},
@@ -311,6 +312,8 @@ def main():
                     help="batched ripple sweep over this many instances instead")
     ap.add_argument("--sweep-steps", type=int, default=64)
     ap.add_argument("--sweep-warmup", type=int, default=16)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="sweep: launch every step's kernels instead of replaying a CUDA graph")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -159,6 +159,15 @@ pic_status pic_sim_create(pic_mesh *m, double dt, double bz_guide, int64_t max_p
 /* Steps between particle re-sorts by triangle (default 16; 0 disables re-sorting). */
 pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
 
+/* Replay steps from a CUDA graph (off by default).  pic_step then records one period of
+ * 2 x the re-sort interval steps (2 with re-sorting off) on an internal stream the first
+ * time it is needed, and launches that graph on the caller's stream for every whole period
+ * that starts at the recorded phase; other steps run as before.  Results are those of plain
+ * steps.  The graph is recorded again after the slot bound or the re-sort interval changed;
+ * per-launch timing (pic_kernel_timing) bypasses it.  Not an operation of the paper: it
+ * removes the host launch cost of small meshes. */
+pic_status pic_sim_set_graph(pic_sim *s, int32_t enable);
+
 /* Set E^n (N1 doubles; PEC entries are forced to 0) and B^{n-1/2} (N2 doubles); either
  * may be NULL to leave it.  Resets the DGL auxiliary flux D = star_eps E. */
 pic_status pic_fields_set(pic_sim *s, const double *E_edges, const double *B_faces_half,

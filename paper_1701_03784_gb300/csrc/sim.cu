@@ -67,6 +67,7 @@ struct SimBase {
     virtual pic_status raw_get(void *dst, int64_t n, cudaStream_t s) = 0;
     virtual pic_status raw_set(const void *src, int64_t n, cudaStream_t s) = 0;
     virtual pic_status step_host(void *state, int64_t n, int64_t steps, cudaStream_t s) = 0;
+    virtual void set_graph(bool on) = 0;
     virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
     virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
     int32_t sort_interval = 16;
@@ -108,6 +109,13 @@ struct SimImpl final : SimBase {
     bool timing_on = false;
     // host round trips (step_host): downloads run on their own stream, chunk by chunk
     static constexpr int RT_CHUNKS = 8;
+    // CUDA-graph replay of whole periods of steps (2 x the re-sort interval: the buffer
+    // parities and the re-sort phase are back where they started)
+    bool use_graph = false, stepped = false;
+    cudaStream_t g_stream = nullptr;
+    cudaGraphExec_t g_exec = nullptr;
+    int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1;
+    int64_t g_bound = -1;
     cudaStream_t rt_stream = nullptr;
     cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr;
     std::vector<cudaEvent_t> ev_free;
@@ -116,6 +124,8 @@ struct SimImpl final : SimBase {
     ~SimImpl() override {
         cudaSetDevice(device);
         cudaDeviceSynchronize();
+        if (g_exec) cudaGraphExecDestroy(g_exec);
+        if (g_stream) cudaStreamDestroy(g_stream);
         if (rt_stream) {
             for (auto e : rt_chunk) cudaEventDestroy(e);
             cudaEventDestroy(rt_step);
@@ -467,11 +477,85 @@ struct SimImpl final : SimBase {
         return PIC_OK;
     }
 
+    void set_graph(bool on) override {
+        use_graph = on;
+        if (!on && g_exec) {
+            cudaGraphExecDestroy(g_exec);
+            g_exec = nullptr;
+        }
+    }
+
     pic_status step(int64_t n, cudaStream_t s) override {
         if (n < 0) {
             set_error("pic_step: negative step count");
             return PIC_ERR_ARG;
         }
+        if (!use_graph || timing_on) return step_direct(n, s);
+        const int64_t L = sort_interval > 0 ? 2 * (int64_t)sort_interval : 2;
+        int64_t done = 0;
+        pic_status st;
+        while (done < n) {
+            const int64_t left = n - done;
+            // a new Gauss-law reference, a first launch (lazy kernel set-up) or a tail
+            // shorter than a period: plain steps
+            if (dgl_dirty || !stepped || left < L) {
+                const int64_t k = (dgl_dirty || !stepped) ? 1 : left;
+                if ((st = step_direct(k, s)) != PIC_OK) return st;
+                done += k;
+                continue;
+            }
+            if (g_exec && (g_bound != n_bound || g_interval != sort_interval)) {
+                cudaGraphExecDestroy(g_exec);
+                g_exec = nullptr;
+            }
+            if (g_exec && (g_cur != cur || g_qcur != qcur || g_since != since_sort)) {
+                // another phase of the period: plain steps until it comes round
+                if ((st = step_direct(1, s)) != PIC_OK) return st;
+                done += 1;
+                continue;
+            }
+            if (!g_exec && (st = capture(L)) != PIC_OK) return st;
+            PIC_CUDA_TRY(cudaGraphLaunch(g_exec, s));
+            n_steps += L;
+            done += L;
+        }
+        return PIC_OK;
+    }
+
+    // record one period of steps, from the current phase, into g_exec (nothing runs)
+    pic_status capture(int64_t L) {
+        if (!g_stream) PIC_CUDA_TRY(cudaStreamCreateWithFlags(&g_stream, cudaStreamNonBlocking));
+        const int64_t n0 = n_steps;
+        g_cur = cur;
+        g_qcur = qcur;
+        g_since = since_sort;
+        g_bound = n_bound;
+        g_interval = sort_interval;
+        PIC_CUDA_TRY(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
+        pic_status st = step_direct(L, g_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(g_stream, &graph);
+        n_steps = n0;
+        if (st != PIC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) {
+            set_error("CUDA error %s: stream capture of the step", cudaGetErrorString(e));
+            return PIC_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&g_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g_exec = nullptr;
+            set_error("CUDA error %s: graph instantiation", cudaGetErrorString(e));
+            return PIC_ERR_CUDA;
+        }
+        return PIC_OK;
+    }
+
+    pic_status step_direct(int64_t n, cudaStream_t s) {
+        stepped = true;
         FieldArgs<P> fa = field_args();
         for (int64_t it = 0; it < n; it++) {
             if (dgl_dirty) {
@@ -901,6 +985,12 @@ extern "C" pic_status pic_sim_create(pic_mesh *pm, double dt, double bz, int64_t
     }
     if (st != PIC_OK) return st;
     *out = s.release();
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sim_set_graph(pic_sim *s, int32_t enable) {
+    SIM_CHECK(s, "pic_sim_set_graph");
+    s->impl->set_graph(enable != 0);
     return PIC_OK;
 }
 

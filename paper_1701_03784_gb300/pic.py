@@ -62,6 +62,7 @@ _SIGS = {
     "pic_spai_get": [_P, _P, _P, _P, _P],
     "pic_sim_create": [_P, _D, _D, _I64, _P],
     "pic_sim_set_sort_interval": [_P, _I32],
+    "pic_sim_set_graph": [_P, _I32],
     "pic_fields_set": [_P, _P, _P, _P],
     "pic_particles_inject": [_P, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _P],
     "pic_step": [_P, _I64, _P],
@@ -258,6 +259,10 @@ def pic_sim_create(mesh, dt, bz_guide=0.0, max_particles=0, torch_memory=True):
 
 def pic_sim_set_sort_interval(sim, interval):
     _check(_lib.pic_sim_set_sort_interval(sim.ptr, interval), "pic_sim_set_sort_interval")
+
+
+def pic_sim_set_graph(sim, enable=True):
+    _check(_lib.pic_sim_set_graph(sim.ptr, 1 if enable else 0), "pic_sim_set_graph")
 
 
 def pic_fields_set(sim, E=None, B=None, stream=None):

@@ -339,3 +339,27 @@ def test_step_host_matches_device_steps(pic, cavity_oracle, prec):
         # the FP64 build sums with floating-point atomics, whose order varies: round-off
         for a, b in [(g1["lam"], g2["lam"]), (g1["u"], g2["u"])] + [(d1[k], d2[k]) for k in "EBJ"]:
             assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_graph_replay_matches_plain_steps(pic, cavity_oracle):
+    """pic_step replaying a CUDA graph of one period (re-sort every 3 steps: 6 steps) gives
+    the state of plain steps, bit for bit in the FP32 build: 45 steps in calls of 1, 7, 13
+    and 24 steps, so that periods start at different phases and tails run plainly."""
+    arrays, oracle = cavity_oracle
+    runs = []
+    for graph in (False, True):
+        o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, 20_000, seed=70,
+                                   sigma_u=0.8, sort_interval=3)
+        pic.pic_sim_set_graph(sim, graph)
+        for k in (1, 7, 13, 24):
+            pic.pic_step(sim, k)
+        d = pic.pic_diagnostics(sim, fields=True)
+        g = pic.pic_particles_get(sim)
+        order = np.argsort(g["pid"])
+        runs.append(({k: g[k][order] for k in ("pid", "tri", "lam", "u")}, d))
+    (g1, d1), (g2, d2) = runs
+    assert d1["n_steps"] == d2["n_steps"] == 45 and d1["n_absorbed"] > 0
+    for k in ("pid", "tri", "lam", "u"):
+        assert np.array_equal(g1[k], g2[k]), k
+    for k in ("E", "B", "J", "n_crossings", "n_absorbed", "dce_nonzero", "dgl_drift"):
+        assert np.array_equal(d1[k], d2[k]), k
