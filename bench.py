@@ -254,6 +254,7 @@ def run_sweep(args):
         pic.pic_sim_set_graph(sim, not args.no_graph)
         pic.pic_fields_set(sim, np.zeros(info["n_edges"]), np.zeros(info["n_tris"]))
         pic.pic_particles_inject(sim, x["z"], x["r"], x["ur"], x["up"], x["uz"], QE, ME, WEIGHT)
+        tuned.append(None if args.no_tune else pic.pic_sim_autotune(sim, 16))
         pic.pic_step(sim, args.sweep_warmup)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -267,6 +268,7 @@ def run_sweep(args):
         return e0.elapsed_time(e1), d
 
     setup_s = time.time() - t_setup
+    tuned = []
     ms_b, d_b = timed(mesh_u, u)
     ms_p = 0.0
     for x in ins:
@@ -287,7 +289,8 @@ def run_sweep(args):
                                % (args.sweep, args.sweep - 1),
                    "instances": args.sweep, "triangles": int(len(u["tris"])),
                    "particles": int(n_part), "dt_s": dt, "sort_interval": args.sort_interval,
-                   "run_steps": SWEEP_RUN_STEPS, "cuda_graph": not args.no_graph},
+                   "run_steps": SWEEP_RUN_STEPS, "cuda_graph": not args.no_graph,
+                   "tuned_batched": tuned[0]},
         "ms_per_step": {"batched": step_b, "plain_sum": step_p},
         "particle_steps_per_s": {"batched": n_part / (step_b * 1e-3),
                                  "plain": n_part / (step_p * 1e-3)},
@@ -312,6 +315,8 @@ def main():
                     help="batched ripple sweep over this many instances instead")
     ap.add_argument("--sweep-steps", type=int, default=64)
     ap.add_argument("--sweep-warmup", type=int, default=16)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the launch-shape autotuner (fixed re-sort interval and shapes)")
     ap.add_argument("--no-graph", action="store_true",
                     help="sweep: launch every step's kernels instead of replaying a CUDA graph")
     args = ap.parse_args()
@@ -354,7 +359,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    # warm-up
+    # launch shapes (re-sort interval, particle-kernel grid, field-kernel block), then warm-up
+    tuned = None if args.no_tune else pic.pic_sim_autotune(sim, 32)
     pic.pic_step(sim, args.warmup)
     barrier()
     n_live = pic.pic_diagnostics(sim)["n_particles"]
@@ -373,8 +379,8 @@ def main():
     push_ms, push_launches = pic.pic_kernel_timing(sim, False)
     diag = pic.pic_diagnostics(sim)
     n_end = diag["n_particles"]
-    resorts = sum(1 for k in range(args.warmup + 1, args.warmup + args.steps + 1)
-                  if args.sort_interval and k % args.sort_interval == 0)
+    si = tuned["sort_interval"] if tuned else args.sort_interval
+    resorts = (args.steps + si - 1) // si if si else 0
     launches = 4 * args.steps + 5 * resorts
 
     # end to end through the C ABI with host buffers: every step uploads the state from
@@ -417,6 +423,7 @@ def main():
                     "h2d_bytes_per_step": n_slots * bpp, "d2h_bytes_per_step": n_slots * bpp,
                     "steps": args.e2e_steps},
             "gpu_launches": launches,
+            "tuning": tuned,
             "clocks": clocks,
             "checks": {"dt_over_stable": dt / dt_max,
                        "dce_nonzero_nodes": diag["dce_nonzero"], "dgl_drift": diag["dgl_drift"],

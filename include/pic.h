@@ -168,6 +168,25 @@ pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
  * removes the host launch cost of small meshes. */
 pic_status pic_sim_set_graph(pic_sim *s, int32_t enable);
 
+/* Launch shapes picked by pic_sim_autotune (not an operation of the paper). */
+typedef struct {
+    int32_t sort_interval;  /* steps between re-sorts by triangle                        */
+    int32_t ctas_per_sm;    /* persistent CTAs per SM of the particle kernel (0: all fit) */
+    int32_t field_block;    /* threads per block of the field kernels                    */
+    int32_t pad;
+    double ms_per_step;     /* device time per step of the chosen setting                */
+} pic_tuning;
+
+/* Autotuner: coordinate descent over the re-sort interval (8, 16, 32), the particle
+ * kernel's CTAs per SM (all that fit, 3, 2) and the field kernels' block size (128, 256,
+ * 512), none of which changes a result (the FP32 state after tuning is bit for bit that
+ * of the same number of plain steps).  Each trial runs trial_steps steps to settle and
+ * trial_steps timed steps: the simulation advances by up to 14 x trial_steps steps.  The
+ * fastest setting stays in effect and is written to *out (may be NULL).  Synchronous.
+ * Errors: PIC_ERR_ARG (trial_steps < 1), CUDA errors of the steps. */
+pic_status pic_sim_autotune(pic_sim *s, int32_t trial_steps, pic_tuning *out,
+                            void *cuda_stream);
+
 /* Set E^n (N1 doubles; PEC entries are forced to 0) and B^{n-1/2} (N2 doubles); either
  * may be NULL to leave it.  Resets the DGL auxiliary flux D = star_eps E. */
 pic_status pic_fields_set(pic_sim *s, const double *E_edges, const double *B_faces_half,

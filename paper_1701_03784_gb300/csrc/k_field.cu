@@ -12,7 +12,7 @@ namespace pic {
 // The same launch clears the step's accumulators (J per edge, Q_abs per node, and in the
 // FP64 build Q^{n+1}, which the particle kernel accumulates).
 template <class P>
-__global__ void __launch_bounds__(256) k_field_b(FieldArgs<P> a) {
+__global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
     using R = typename P::R;
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f < a.N1) a.J[f] = 0;
@@ -103,7 +103,7 @@ __device__ __forceinline__ void node_update(const FieldArgs<P> &a, int64_t k) {
 // K4a, one thread per free edge: r = D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}; the DGL
 // auxiliary flux D += dt r.  The same launch does the per-node update (thread k, node k).
 template <class P>
-__global__ void __launch_bounds__(256) k_field_r(FieldArgs<P> a) {
+__global__ void __launch_bounds__(512) k_field_r(FieldArgs<P> a) {
     using R = typename P::R;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.N0) node_update<P>(a, i);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_field_r(FieldArgs<P> a) {
 // K4b, sliced ELL SpMV over free edges: E_e += dt (M r)_i.  A warp owns a slice of 32 rows
 // stored column-major, so each step of the row loop reads 32 consecutive values.
 template <class P>
-__global__ void __launch_bounds__(256) k_field_spmv(FieldArgs<P> a) {
+__global__ void __launch_bounds__(512) k_field_spmv(FieldArgs<P> a) {
     using R = typename P::R;
     int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t slice = row >> 5;
@@ -151,15 +151,17 @@ __global__ void __launch_bounds__(256) k_field_spmv(FieldArgs<P> a) {
 template <class P>
 void launch_field_b(const FieldArgs<P> &a, cudaStream_t s) {
     const int64_t n = std::max(a.N2, std::max(a.N1, a.N0));
-    k_field_b<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+    const int b = a.block;
+    k_field_b<P><<<(unsigned)((n + b - 1) / b), b, 0, s>>>(a);
 }
 
 template <class P>
 void launch_field_e(const FieldArgs<P> &a, cudaStream_t s) {
     const int64_t n = std::max(a.nf, a.N0);
-    k_field_r<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+    const int b = a.block;
+    k_field_r<P><<<(unsigned)((n + b - 1) / b), b, 0, s>>>(a);
     int64_t rows = ((a.nf + 31) / 32) * 32;
-    k_field_spmv<P><<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(a);
+    k_field_spmv<P><<<(unsigned)((rows + b - 1) / b), b, 0, s>>>(a);
 }
 
 template void launch_field_b<PF32>(const FieldArgs<PF32> &, cudaStream_t);

@@ -562,7 +562,8 @@ void launch_push_f32(const PushArgs<PF32> &a, int64_t n_bound, cudaStream_t s) {
         ps.sms = sms > 0 ? sms : 1;
     }
     const int64_t tiles = (n_bound + TILE - 1) / TILE;
-    const int64_t grid = std::min<int64_t>(tiles, (int64_t)ps.sms * ps.bps);
+    const int bps = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, ps.bps) : ps.bps;
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)ps.sms * bps);
     k_push_f32<<<(unsigned)grid, NT, smem, s>>>(a);
 }
 

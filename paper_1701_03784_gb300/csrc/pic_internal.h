@@ -177,6 +177,7 @@ struct PushArgs {
     typename P::R inv_c2;
     typename P::R bz;
     int32_t walk_cap;
+    int32_t ctas_per_sm;        // launch shape: persistent CTAs per SM (0: as many as fit)
 };
 
 template <class P>
@@ -207,6 +208,7 @@ struct FieldArgs {
     typename P::Acc *Qwall;     // N0: charge removed at walls since the Gauss-law reference
     unsigned long long *counters;
     int64_t N0;
+    int32_t block;              // launch shape: threads per block (<= 512)
 };
 
 template <class P> void launch_push(const PushArgs<P> &a, int64_t n_bound, cudaStream_t s);

@@ -68,6 +68,7 @@ struct SimBase {
     virtual pic_status raw_set(const void *src, int64_t n, cudaStream_t s) = 0;
     virtual pic_status step_host(void *state, int64_t n, int64_t steps, cudaStream_t s) = 0;
     virtual void set_graph(bool on) = 0;
+    virtual pic_status autotune(int32_t trial, pic_tuning *out, cudaStream_t s) = 0;
     virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
     virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
     int32_t sort_interval = 16;
@@ -112,6 +113,9 @@ struct SimImpl final : SimBase {
     // CUDA-graph replay of whole periods of steps (2 x the re-sort interval: the buffer
     // parities and the re-sort phase are back where they started)
     bool use_graph = false, stepped = false;
+    // launch shapes chosen by autotune: persistent CTAs per SM of the particle kernel
+    // (0: as many as fit) and threads per block of the field kernels
+    int32_t tune_ctas = 0, tune_block = 256;
     cudaStream_t g_stream = nullptr;
     cudaGraphExec_t g_exec = nullptr;
     int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1;
@@ -340,6 +344,7 @@ struct SimImpl final : SimBase {
         a.Qwall = Qwall;
         a.counters = counters;
         a.N0 = m->N0;
+        a.block = tune_block;
         return a;
     }
 
@@ -522,6 +527,67 @@ struct SimImpl final : SimBase {
         return PIC_OK;
     }
 
+    // Launch-shape autotuner.  Coordinate descent over three knobs that change no result
+    // (a re-sort only reorders slots, and the kernels' arithmetic does not depend on the
+    // grid or the block size): the re-sort interval, the particle kernel's CTAs per SM
+    // and the field kernels' block size.  Each trial runs `trial` steps to settle and
+    // `trial` timed steps (CUDA events on the stream); the simulation advances through all
+    // of them.  Keeps the fastest setting.
+    pic_status autotune(int32_t trial, pic_tuning *out, cudaStream_t s) override {
+        if (trial < 1) {
+            set_error("pic_sim_autotune: trial length must be positive");
+            return PIC_ERR_ARG;
+        }
+        const bool graph = use_graph;
+        use_graph = false;
+        cudaEvent_t e0, e1;
+        PIC_CUDA_TRY(cudaEventCreate(&e0));
+        PIC_CUDA_TRY(cudaEventCreate(&e1));
+        pic_status st = PIC_OK;
+        auto run = [&](double &ms) -> pic_status {
+            pic_status r;
+            if ((r = step_direct(trial, s)) != PIC_OK) return r;
+            PIC_CUDA_TRY(cudaEventRecord(e0, s));
+            if ((r = step_direct(trial, s)) != PIC_OK) return r;
+            PIC_CUDA_TRY(cudaEventRecord(e1, s));
+            PIC_CUDA_TRY(cudaEventSynchronize(e1));
+            float x = 0;
+            PIC_CUDA_TRY(cudaEventElapsedTime(&x, e0, e1));
+            ms = x / trial;
+            return PIC_OK;
+        };
+        double best = 0;
+        st = run(best);
+        const int32_t sorts[] = {8, 16, 32}, ctas[] = {0, 3, 2}, blocks[] = {128, 256, 512};
+        int32_t *knob[] = {&sort_interval, &tune_ctas, &tune_block};
+        const int32_t *cand[] = {sorts, ctas, blocks};
+        for (int k = 0; k < 3 && st == PIC_OK; k++) {
+            const int32_t keep = *knob[k];
+            int32_t choice = keep;
+            for (int c = 0; c < 3 && st == PIC_OK; c++) {
+                if (cand[k][c] == keep) continue;
+                *knob[k] = cand[k][c];
+                double ms = 0;
+                if ((st = run(ms)) == PIC_OK && ms < best) {
+                    best = ms;
+                    choice = cand[k][c];
+                }
+            }
+            *knob[k] = choice;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        use_graph = graph;
+        if (st != PIC_OK) return st;
+        if (out) {
+            out->sort_interval = sort_interval;
+            out->ctas_per_sm = tune_ctas;
+            out->field_block = tune_block;
+            out->ms_per_step = best;
+        }
+        return PIC_OK;
+    }
+
     // record one period of steps, from the current phase, into g_exec (nothing runs)
     pic_status capture(int64_t L) {
         if (!g_stream) PIC_CUDA_TRY(cudaStreamCreateWithFlags(&g_stream, cudaStreamNonBlocking));
@@ -584,6 +650,7 @@ struct SimImpl final : SimBase {
             pa.inv_c2 = (R)(1.0 / (m->units.c * m->units.c));
             pa.bz = (R)bz;
             pa.walk_cap = m->units.walk_cap;
+            pa.ctas_per_sm = tune_ctas;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (timing_on) {
                 e0 = take_event();
@@ -986,6 +1053,12 @@ extern "C" pic_status pic_sim_create(pic_mesh *pm, double dt, double bz, int64_t
     if (st != PIC_OK) return st;
     *out = s.release();
     return PIC_OK;
+}
+
+extern "C" pic_status pic_sim_autotune(pic_sim *s, int32_t trial_steps, pic_tuning *out,
+                                       void *st) {
+    SIM_CHECK(s, "pic_sim_autotune");
+    return s->impl->autotune(trial_steps, out, (cudaStream_t)st);
 }
 
 extern "C" pic_status pic_sim_set_graph(pic_sim *s, int32_t enable) {

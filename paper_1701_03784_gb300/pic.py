@@ -63,6 +63,7 @@ _SIGS = {
     "pic_sim_create": [_P, _D, _D, _I64, _P],
     "pic_sim_set_sort_interval": [_P, _I32],
     "pic_sim_set_graph": [_P, _I32],
+    "pic_sim_autotune": [_P, _I32, _P, _P],
     "pic_fields_set": [_P, _P, _P, _P],
     "pic_particles_inject": [_P, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _P],
     "pic_step": [_P, _I64, _P],
@@ -263,6 +264,21 @@ def pic_sim_set_sort_interval(sim, interval):
 
 def pic_sim_set_graph(sim, enable=True):
     _check(_lib.pic_sim_set_graph(sim.ptr, 1 if enable else 0), "pic_sim_set_graph")
+
+
+class pic_tuning(ctypes.Structure):
+    _fields_ = [("sort_interval", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("field_block", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_double)]
+
+
+def pic_sim_autotune(sim, trial_steps=32, stream=None):
+    """Pick the launch shapes (re-sort interval, particle-kernel CTAs per SM, field-kernel
+    block size) by timing trial steps; the simulation advances by up to 14 x trial_steps."""
+    t = pic_tuning()
+    _check(_lib.pic_sim_autotune(sim.ptr, int(trial_steps), ctypes.byref(t), _stream(stream)),
+           "pic_sim_autotune")
+    return {k: getattr(t, k) for k, _ in pic_tuning._fields_ if k != "pad"}
 
 
 def pic_fields_set(sim, E=None, B=None, stream=None):

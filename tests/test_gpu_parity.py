@@ -363,3 +363,33 @@ def test_graph_replay_matches_plain_steps(pic, cavity_oracle):
         assert np.array_equal(g1[k], g2[k]), k
     for k in ("E", "B", "J", "n_crossings", "n_absorbed", "dce_nonzero", "dgl_drift"):
         assert np.array_equal(d1[k], d2[k]), k
+
+
+def test_autotune_changes_no_result(pic, cavity_oracle):
+    """pic_sim_autotune tries re-sort intervals, particle-kernel grids and field-kernel block
+    sizes while stepping: the FP32 state after it is bit for bit that of the same number
+    of plain steps (14 trials of 8 steps)."""
+    arrays, oracle = cavity_oracle
+    runs = []
+    for tune in (True, False):
+        o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, 20_000, seed=80,
+                                   sigma_u=0.8, sort_interval=16)
+        if tune:
+            t = pic.pic_sim_autotune(sim, 8)
+            assert t["sort_interval"] in (8, 16, 32) and t["ctas_per_sm"] in (0, 2, 3)
+            assert t["field_block"] in (128, 256, 512) and t["ms_per_step"] > 0
+        else:
+            pic.pic_step(sim, 14 * 8)
+        d = pic.pic_diagnostics(sim, fields=True)
+        g = pic.pic_particles_get(sim)
+        # removed particles keep their slots until a re-sort, and the runs re-sort at
+        # different steps: compare the live ones
+        live = np.nonzero(g["tri"] >= 0)[0]
+        order = live[np.argsort(g["pid"][live])]
+        runs.append(({k: g[k][order] for k in ("pid", "tri", "lam", "u")}, d))
+    (g1, d1), (g2, d2) = runs
+    assert d1["n_steps"] == d2["n_steps"] == 112
+    for k in ("pid", "tri", "lam", "u"):
+        assert np.array_equal(g1[k], g2[k]), k
+    for k in ("E", "B", "J", "n_crossings", "n_absorbed", "dce_nonzero"):
+        assert np.array_equal(d1[k], d2[k]), k
