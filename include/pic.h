@@ -274,6 +274,43 @@ pic_status pic_step_host(pic_sim *s, void *host_state, int64_t n_slots, int64_t 
 pic_status pic_kernel_timing(pic_sim *s, int32_t enable, double *push_ms, int64_t *launches,
                              void *cuda_stream);
 
+/* ---- Surrogate network ensemble (not in the paper) ------------------------------------
+ * An ensemble of n_members multilayer perceptrons with layer widths sizes[0..n_layers]
+ * (inputs first): hidden layers z = x W^T + b followed by the tanh form of GELU, a linear
+ * output layer; trained on mean-squared error with Adam.  It stands in for the simulation
+ * where the members agree (the caller gates on their spread).  Parameters per member: for
+ * each layer W (n_out x n_in, row-major) then b (n_out), members one after another.
+ * Device memory comes from the allocator hook, like the simulations'.  max_batch bounds
+ * the training batch and the rows of pic_mlp_grad; inference is chunked. */
+typedef struct pic_mlp pic_mlp;
+pic_status pic_mlp_create(int32_t n_members, int32_t n_layers, const int32_t *sizes,
+                          int32_t max_batch, pic_mlp **out);
+pic_status pic_mlp_param_count(pic_mlp *m, int64_t *per_member);
+/* Host copies of all members' parameters (n_members x per_member doubles; stored as FP32).
+ * Setting resets the Adam moments.  Synchronous. */
+pic_status pic_mlp_params_set(pic_mlp *m, const double *params);
+pic_status pic_mlp_params_get(pic_mlp *m, double *params);
+/* steps Adam steps (learning rate lr, moments 0.9 / 0.999) on minibatches of `batch` rows
+ * drawn with replacement from the n training rows X (device, n x inputs, FP32) and T
+ * (device, n x outputs, FP32) by a counter-based hash of (seed, member, step, row): each
+ * member sees its own draws.  last_loss (host, n_members, may be NULL) receives each
+ * member's loss on its last minibatch; then the call is synchronous. */
+pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *T, int64_t n, int32_t batch,
+                         int64_t steps, double lr, uint64_t seed, double *last_loss,
+                         void *cuda_stream);
+/* Gradient of every member's loss over the n <= max_batch rows X, T (device) at the current
+ * parameters, to host doubles (n_members x per_member), and the losses (may be NULL).
+ * Synchronous.  For checking the backward pass. */
+pic_status pic_mlp_grad(pic_mlp *m, const float *X, const float *T, int64_t n, double *grads,
+                        double *loss, void *cuda_stream);
+/* Outputs Y (device, n_members x n x outputs, FP32) for the rows X (device, n x inputs,
+ * FP32).  tensor_cores = 0: FP32 on CUDA cores.  tensor_cores = 1: BF16 operands and FP32
+ * accumulation on the tensor cores (tcgen05, every width at most 256; PIC_ERR_ARG
+ * otherwise; synchronous, PIC_ERR_TIMEOUT if a bounded wait gave up). */
+pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int64_t n, int32_t tensor_cores,
+                           void *cuda_stream);
+void pic_mlp_destroy(pic_mlp *m);
+
 void pic_sim_destroy(pic_sim *s);
 void pic_mesh_destroy(pic_mesh *m);
 const char *pic_last_error(void);

@@ -1,0 +1,261 @@
+// Surrogate network inference on the 5th-generation tensor cores: BF16 operands in shared
+// memory, FP32 accumulation in tensor memory (TMEM).
+//
+// One CTA of 128 threads takes 128 samples of one ensemble member through every layer:
+//  * the activations (128 x K) and the layer's weights (N x K) sit in shared memory in the
+//    no-swizzle K-major layout (8 x 8 core matrices of 16-byte rows, K-adjacent core
+//    matrices 128 bytes apart, 8-row groups K/8 x 128 bytes apart);
+//  * one thread issues tcgen05.mma (kind::f16, M = 128, N = the padded layer width), 16
+//    of K at a time, accumulating a 128 x N FP32 tile in TMEM, and commits to an mbarrier;
+//  * each warp reads its 32 TMEM lanes (sample rows) with tcgen05.ld, adds the bias,
+//    applies the tanh-GELU (hidden layers) and writes the next layer's BF16 operand back
+//    into shared memory, or writes the FP32 outputs.
+// Every mbarrier wait is bounded (timeout counted, TMEM still freed).
+#include <cuda_bf16.h>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+namespace {
+constexpr int TM = 128;       // samples per CTA = MMA M
+constexpr int NTH = 128;      // 4 warps: one TMEM lane quadrant each
+constexpr int KMAX = 256;
+constexpr int NMAX = 256;
+constexpr int TMEM_COLS = 256;
+constexpr long long WAIT_LIMIT = 1LL << 22;
+constexpr float C_GELU = 0.7978845608028654f;   // sqrt(2/pi)
+
+struct TcSmem {
+    uint16_t a[TM * KMAX];     // activations, core-matrix layout
+    uint16_t w[NMAX * KMAX];   // weights of the current layer, core-matrix layout
+    float bias[NMAX];
+    unsigned long long mbar;
+    unsigned int tmem;
+};
+
+// element offset of (row r, column k) in a core-matrix tile with kp (padded) columns
+__host__ __device__ __forceinline__ int core_off(int r, int k, int kp) {
+    return ((r >> 3) * (kp >> 3) * 64) + ((k >> 3) * 64) + ((r & 7) * 8) + (k & 7);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) |
+           ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ULL << 46);
+}
+// instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N and M = 128
+__device__ __forceinline__ unsigned idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) |
+           ((unsigned)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_bf16(unsigned d, unsigned long long a, unsigned long long b,
+                                         unsigned idesc, int accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
+    for (long long k = 0; k < WAIT_LIMIT; k++) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float gelu(float z) {
+    return 0.5f * z * (1.f + tanhf(C_GELU * (z + 0.044715f * z * z * z)));
+}
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+// 8 values as 8 BF16 in one 16-byte word (element 0 lowest)
+__device__ __forceinline__ uint4 pack8(const float *v) {
+    uint4 q;
+    q.x = (unsigned)bf16_bits(v[0]) | ((unsigned)bf16_bits(v[1]) << 16);
+    q.y = (unsigned)bf16_bits(v[2]) | ((unsigned)bf16_bits(v[3]) << 16);
+    q.z = (unsigned)bf16_bits(v[4]) | ((unsigned)bf16_bits(v[5]) << 16);
+    q.w = (unsigned)bf16_bits(v[6]) | ((unsigned)bf16_bits(v[7]) << 16);
+    return q;
+}
+
+__global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, float *Y,
+                                                   long long n) {
+    extern __shared__ unsigned char raw[];
+    const unsigned pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
+    TcSmem &sm = *reinterpret_cast<TcSmem *>(raw + pad);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int z = blockIdx.y;
+    const long long row = (long long)blockIdx.x * TM + tid;
+
+    if (tid == 0) mbar_init(&sm.mbar, 1);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&sm.tmem)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // layer-0 operand: this thread's sample, BF16, zero-padded to kp[0] columns
+    {
+        const int k0 = tc.k[0], kp = tc.kp[0];
+        for (int c = 0; c < kp; c += 8) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int kk = c + j;
+                v[j] = row < n && kk < k0 ? X[row * k0 + kk] : 0.f;
+            }
+            *reinterpret_cast<uint4 *>(sm.a + core_off(tid, c, kp)) = pack8(v);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = sm.tmem;
+    const unsigned lane_base = (unsigned)(warp * 32) << 16;
+
+    for (int l = 0; l < tc.L; l++) {
+        const int kp = tc.kp[l], np = tc.np[l];
+        const bool last = l == tc.L - 1;
+        // the layer's weights (already in core-matrix layout) and bias
+        const uint4 *src = reinterpret_cast<const uint4 *>(tc.w + (long long)z * tc.wmember + tc.woff[l]);
+        uint4 *dst = reinterpret_cast<uint4 *>(sm.w);
+        const int n16 = np * kp / 8;
+        for (int i = tid; i < n16; i += NTH) dst[i] = src[i];
+        for (int i = tid; i < np; i += NTH) sm.bias[i] = tc.b[(long long)z * tc.bmember + tc.boff[l] + i];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const unsigned a0 = smem_u32(sm.a), w0 = smem_u32(sm.w);
+            const unsigned sbo = (unsigned)kp / 8u * 128u;
+            const unsigned id = idesc_bf16(np);
+            for (int kk = 0; kk < kp / 16; kk++)
+                mma_bf16(tmem, sdesc(a0 + kk * 256u, 128u, sbo), sdesc(w0 + kk * 256u, 128u, sbo),
+                         id, kk > 0);
+            mma_commit(&sm.mbar);
+        }
+        const bool ok = mbar_wait(&sm.mbar, (unsigned)(l & 1));
+        if (!__syncthreads_and(ok)) {
+            // the products did not complete in time: count it, give them one more bounded
+            // wait, free TMEM below
+            if (tid == 0) {
+                atomicAdd(tc.err, 1u);
+                mbar_wait(&sm.mbar, (unsigned)(l & 1));
+            }
+            __syncthreads();
+            break;
+        }
+        fence_after();
+        for (int c = 0; c < np; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + (unsigned)c, v);
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] += sm.bias[c + j];
+            if (!last) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) v[j] = gelu(v[j]);
+                *reinterpret_cast<uint4 *>(sm.a + core_off(tid, c, np)) = pack8(v);
+                *reinterpret_cast<uint4 *>(sm.a + core_off(tid, c + 8, np)) = pack8(v + 8);
+            } else if (row < n) {
+                const int nout = tc.n[l];
+#pragma unroll
+                for (int j = 0; j < 16; j++)
+                    if (c + j < nout) Y[((long long)z * n + row) * nout + c + j] = v[j];
+            }
+        }
+        fence_before();
+        __syncthreads();
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS) : "memory");
+}
+
+// FP32 parameters -> BF16 core-matrix weights and FP32 biases, zero-padded
+struct PackArgs {
+    long long woff[MLP_MAX_LAYERS], boff[MLP_MAX_LAYERS];
+};
+__global__ void k_mlp_pack(MlpTc tc, const float *params, long long P, PackArgs pa) {
+    const int z = blockIdx.y / tc.L, l = blockIdx.y % tc.L;
+    const int kp = tc.kp[l], np = tc.np[l], k = tc.k[l], nn = tc.n[l];
+    const float *W = params + (long long)z * P + pa.woff[l];
+    uint16_t *dst = tc.w + (long long)z * tc.wmember + tc.woff[l];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np * kp; i += gridDim.x * blockDim.x) {
+        const int r = i / kp, c = i % kp;
+        dst[core_off(r, c, kp)] = bf16_bits(r < nn && c < k ? W[(long long)r * k + c] : 0.f);
+    }
+    const float *b = params + (long long)z * P + pa.boff[l];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
+        tc.b[(long long)z * tc.bmember + tc.boff[l] + i] = i < nn ? b[i] : 0.f;
+}
+}  // namespace
+
+void mlp_tc_pack(const MlpTc &tc, const float *params, long long P, const long long *woff,
+                 const long long *boff, cudaStream_t s) {
+    PackArgs pa;
+    for (int l = 0; l < tc.L; l++) {
+        pa.woff[l] = woff[l];
+        pa.boff[l] = boff[l];
+    }
+    k_mlp_pack<<<dim3(64, tc.E * tc.L), 256, 0, s>>>(tc, params, P, pa);
+}
+
+pic_status mlp_tc_forward(const MlpTc &tc, const float *X, float *Y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return PIC_OK;
+    const int smem = (int)sizeof(TcSmem) + 1024;
+    PIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PIC_CUDA_TRY(cudaMemsetAsync(tc.err, 0, sizeof(unsigned int), s));
+    dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)tc.E);
+    k_mlp_tc<<<grid, NTH, smem, s>>>(tc, X, Y, (long long)n);
+    PIC_CUDA_TRY(cudaGetLastError());
+    unsigned int err = 0;
+    PIC_CUDA_TRY(cudaMemcpyAsync(&err, tc.err, sizeof(err), cudaMemcpyDeviceToHost, s));
+    PIC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) {
+        set_error("pic_mlp_forward: %u tensor-core waits timed out", err);
+        return PIC_ERR_TIMEOUT;
+    }
+    return PIC_OK;
+}
+
+}  // namespace pic

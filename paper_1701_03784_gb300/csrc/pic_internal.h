@@ -18,6 +18,36 @@ namespace pic {
 // errors
 // ---------------------------------------------------------------------------------
 void set_error(const char *fmt, ...);
+
+// device-memory hooks installed by pic_set_allocator (nulls: cudaMalloc / cudaFree)
+struct Allocator {
+    pic_alloc_fn alloc = nullptr;
+    pic_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+Allocator current_allocator();
+
+// Tensor-core inference state of a surrogate network (k_mlp_tc.cu): BF16 weights of every
+// member and layer, zero-padded to multiples of 16 and stored in the tensor core's
+// no-swizzle K-major layout (8 x 8 core matrices, K-adjacent ones contiguous), and FP32
+// biases.  Usable when every layer width is at most 256.
+constexpr int MLP_MAX_LAYERS = 16;
+struct MlpTc {
+    int E = 0, L = 0;
+    int k[MLP_MAX_LAYERS] = {}, n[MLP_MAX_LAYERS] = {};    // widths: in, out
+    int kp[MLP_MAX_LAYERS] = {}, np[MLP_MAX_LAYERS] = {};  // padded to multiples of 16
+    long long woff[MLP_MAX_LAYERS] = {}, boff[MLP_MAX_LAYERS] = {};
+    long long wmember = 0, bmember = 0;                     // elements per member
+    uint16_t *w = nullptr;                                  // E * wmember BF16
+    float *b = nullptr;                                     // E * bmember
+    unsigned int *err = nullptr;                            // bounded-wait timeouts
+    bool ok = false;
+};
+// FP32 parameters (per member: W_l (n x k), b_l at woff / boff, member stride P) -> tc
+void mlp_tc_pack(const MlpTc &tc, const float *params, long long P, const long long *woff,
+                 const long long *boff, cudaStream_t s);
+// Y (E x n x outputs, FP32) from X (n x inputs, FP32); PIC_ERR_TIMEOUT if a wait gave up
+pic_status mlp_tc_forward(const MlpTc &tc, const float *X, float *Y, int64_t n, cudaStream_t s);
 #define PIC_CUDA_TRY(expr)                                                              \
     do {                                                                                \
         cudaError_t err__ = (expr);                                                     \

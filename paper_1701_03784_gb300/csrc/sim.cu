@@ -9,13 +9,13 @@
 
 namespace pic {
 
-struct Allocator {
-    pic_alloc_fn alloc = nullptr;
-    pic_free_fn free = nullptr;
-    void *ctx = nullptr;
-};
 static Allocator g_allocator;
 static std::mutex g_allocator_mu;
+
+Allocator current_allocator() {
+    std::lock_guard<std::mutex> lk(g_allocator_mu);
+    return g_allocator;
+}
 
 // Scratch of pic_charges_get_static: a fixed device array instead of an allocation, for
 // callers that must not allocate device memory.  Every GPU that loads the library holds

@@ -64,6 +64,13 @@ _SIGS = {
     "pic_sim_set_sort_interval": [_P, _I32],
     "pic_sim_set_graph": [_P, _I32],
     "pic_sim_autotune": [_P, _I32, _P, _P],
+    "pic_mlp_create": [_I32, _I32, _P, _I32, _P],
+    "pic_mlp_param_count": [_P, _P],
+    "pic_mlp_params_set": [_P, _P],
+    "pic_mlp_params_get": [_P, _P],
+    "pic_mlp_train": [_P, _P, _P, _I64, _I32, _I64, _D, ctypes.c_uint64, _P, _P],
+    "pic_mlp_grad": [_P, _P, _P, _I64, _P, _P, _P],
+    "pic_mlp_forward": [_P, _P, _P, _I64, _I32, _P],
     "pic_fields_set": [_P, _P, _P, _P],
     "pic_particles_inject": [_P, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _P],
     "pic_step": [_P, _I64, _P],
@@ -88,8 +95,11 @@ _lib.pic_sim_destroy.argtypes = [_P]
 _lib.pic_sim_destroy.restype = None
 _lib.pic_mesh_destroy.argtypes = [_P]
 _lib.pic_mesh_destroy.restype = None
+_lib.pic_mlp_destroy.argtypes = [_P]
+_lib.pic_mlp_destroy.restype = None
 
-EXPORTED = sorted(list(_SIGS) + ["pic_last_error", "pic_sim_destroy", "pic_mesh_destroy"])
+EXPORTED = sorted(list(_SIGS) + ["pic_last_error", "pic_sim_destroy", "pic_mesh_destroy",
+                                  "pic_mlp_destroy"])
 
 
 def _check(status, where):
@@ -397,3 +407,79 @@ def pic_mesh_destroy(mesh):
     if mesh.ptr:
         _lib.pic_mesh_destroy(mesh.ptr)
         mesh.ptr = None
+
+
+# ---- surrogate network ensemble ------------------------------------------------------------
+
+class Mlp:
+    def __init__(self, ptr, members, sizes):
+        self.ptr = ptr
+        self.members = members
+        self.sizes = tuple(sizes)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            _lib.pic_mlp_destroy(self.ptr)
+            self.ptr = None
+
+
+def _dev(t, what):
+    """Address of a contiguous FP32 CUDA tensor."""
+    import torch
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous(), what
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pic_mlp_create(n_members, sizes, max_batch):
+    sz = np.ascontiguousarray(sizes, dtype=np.int32)
+    out = _P()
+    _check(_lib.pic_mlp_create(int(n_members), len(sz) - 1, _ptr(sz), int(max_batch),
+                               ctypes.byref(out)), "pic_mlp_create")
+    return Mlp(out, int(n_members), sz)
+
+
+def pic_mlp_param_count(m):
+    n = ctypes.c_int64()
+    _check(_lib.pic_mlp_param_count(m.ptr, ctypes.byref(n)), "pic_mlp_param_count")
+    return n.value
+
+
+def pic_mlp_params_set(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    assert p.size == m.members * pic_mlp_param_count(m)
+    _check(_lib.pic_mlp_params_set(m.ptr, _ptr(p)), "pic_mlp_params_set")
+
+
+def pic_mlp_params_get(m):
+    p = np.zeros((m.members, pic_mlp_param_count(m)))
+    _check(_lib.pic_mlp_params_get(m.ptr, _ptr(p)), "pic_mlp_params_get")
+    return p
+
+
+def pic_mlp_train(m, X, T, batch, steps, lr=1e-3, seed=0, stream=None):
+    """Adam steps on minibatches of the device rows X (n x in) and T (n x out); returns each
+    member's loss on its last minibatch."""
+    loss = np.zeros(m.members)
+    _check(_lib.pic_mlp_train(m.ptr, _dev(X, "X"), _dev(T, "T"), X.shape[0], int(batch),
+                              int(steps), float(lr), int(seed), _ptr(loss), _stream(stream)),
+           "pic_mlp_train")
+    return loss
+
+
+def pic_mlp_grad(m, X, T, stream=None):
+    g = np.zeros((m.members, pic_mlp_param_count(m)))
+    loss = np.zeros(m.members)
+    _check(_lib.pic_mlp_grad(m.ptr, _dev(X, "X"), _dev(T, "T"), X.shape[0], _ptr(g), _ptr(loss),
+                             _stream(stream)), "pic_mlp_grad")
+    return g, loss
+
+
+def pic_mlp_forward(m, X, tensor_cores=False, out=None, stream=None):
+    """Device outputs (members x n x out, FP32) for the device rows X (n x in)."""
+    import torch
+    n = X.shape[0]
+    Y = out if out is not None else torch.empty((m.members, n, int(m.sizes[-1])),
+                                                 dtype=torch.float32, device=X.device)
+    _check(_lib.pic_mlp_forward(m.ptr, _dev(X, "X"), _dev(Y, "Y"), n, 1 if tensor_cores else 0,
+                                _stream(stream)), "pic_mlp_forward")
+    return Y
