@@ -408,6 +408,40 @@ def run_surrogate(args):
     return 0
 
 
+def run_mlp_queries(args):
+    """Inference of a 5-member ensemble (random parameters, the surrogate's widths) on
+    args.mlp_queries rows: tensor cores and CUDA cores, CUDA events, 10 launches each."""
+    import torch
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import pic, surrogate as S
+    ens = S.Ensemble(5, S.SIZES, max_batch=256, seed=9)
+    n = args.mlp_queries
+    q = torch.tensor(np.random.default_rng(5).uniform(-1, 1, (n, 6)), dtype=torch.float32,
+                     device="cuda")
+    Y = torch.empty((5, n, S.SIZES[-1]), dtype=torch.float32, device="cuda")
+    flop = 5 * n * 2 * sum(a * b for a, b in zip(S.SIZES[:-1], S.SIZES[1:]))
+    ms = {}
+    for tc in (True, False):
+        pic.pic_mlp_forward(ens.net, q, tensor_cores=tc, out=Y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            pic.pic_mlp_forward(ens.net, q, tensor_cores=tc, out=Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms["tensor_cores" if tc else "cuda_cores"] = e0.elapsed_time(e1) / 10
+    peak, kind = measured_peak("bf16_tflops")
+    tf = flop / (ms["tensor_cores"] * 1e-3) / 1e12
+    print(json.dumps({"metric": "surrogate queries/s (5-member ensemble)",
+                      "value": n / (ms["tensor_cores"] * 1e-3), "unit": "queries/s",
+                      "ms": ms, "roofline": {"bound": "tensor", "achieved": tf, "peak": peak,
+                                             "unit": "TFLOP/s", "frac": tf / peak,
+                                             "peak_kind": kind, "flop_per_launch": flop}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,6 +460,8 @@ def main():
     ap.add_argument("--surrogate", type=int, default=0,
                     help="surrogate of the sweep trained on this many batched PIC runs instead")
     ap.add_argument("--surrogate-steps", type=int, default=4000)
+    ap.add_argument("--mlp-queries", type=int, default=0,
+                    help="time surrogate-network inference on this many queries instead")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the launch-shape autotuner (fixed re-sort interval and shapes)")
     ap.add_argument("--no-graph", action="store_true",
@@ -437,6 +473,8 @@ def main():
         return run_sweep(args)
     if args.surrogate:
         return run_surrogate(args)
+    if args.mlp_queries:
+        return run_mlp_queries(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

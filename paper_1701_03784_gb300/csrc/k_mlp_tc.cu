@@ -19,7 +19,7 @@ namespace pic {
 
 namespace {
 constexpr int TM = 128;       // samples per CTA = MMA M
-constexpr int NTH = 128;      // 4 warps: one TMEM lane quadrant each
+constexpr int NTH = 256;      // 8 warps: two per TMEM lane quadrant, each half the columns
 constexpr int KMAX = 256;
 constexpr int NMAX = 256;
 constexpr int TMEM_COLS = 256;
@@ -29,8 +29,9 @@ constexpr float C_GELU = 0.7978845608028654f;   // sqrt(2/pi)
 struct TcSmem {
     uint16_t a[TM * KMAX];     // activations, core-matrix layout
     uint16_t w[NMAX * KMAX];   // weights of the current layer, core-matrix layout
-    float bias[NMAX];
-    unsigned long long mbar;
+    float bias[2][NMAX];       // biases of the current and the next layer
+    unsigned long long mbar;   // products of a layer done
+    unsigned long long wbar;   // weights and bias of a layer landed
     unsigned int tmem;
 };
 
@@ -102,8 +103,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity
     return false;
 }
 
-__device__ __forceinline__ float gelu(float z) {
-    return 0.5f * z * (1.f + tanhf(C_GELU * (z + 0.044715f * z * z * z)));
+// tanh-GELU with the hardware tanh approximation (relative error about 2^-11, below the
+// BF16 rounding of the result)
+__device__ __forceinline__ float gelu_approx(float z) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(C_GELU * (z + 0.044715f * z * z * z)));
+    return 0.5f * z * (1.f + t);
+}
+// 1-D bulk copy global -> shared completing on an mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ uint16_t bf16_bits(float x) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -117,24 +129,45 @@ __device__ __forceinline__ uint4 pack8(const float *v) {
     q.w = (unsigned)bf16_bits(v[6]) | ((unsigned)bf16_bits(v[7]) << 16);
     return q;
 }
+// one thread: fetch layer l's weights (core-matrix layout, np x kp BF16) and bias (np FP32,
+// into bias buffer l % 2), completing on wbar
+__device__ __forceinline__ void load_layer(const MlpTc &tc, TcSmem &sm, int z, int l) {
+    const unsigned wb = (unsigned)(tc.np[l] * tc.kp[l] * 2), bb = (unsigned)(tc.np[l] * 4);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(&sm.wbar)), "r"(wb + bb) : "memory");
+    bulk_load(sm.w, tc.w + (long long)z * tc.wmember + tc.woff[l], wb, &sm.wbar);
+    bulk_load(sm.bias[l & 1], tc.b + (long long)z * tc.bmember + tc.boff[l], bb, &sm.wbar);
+}
 
 __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, float *Y,
                                                    long long n) {
     extern __shared__ unsigned char raw[];
     const unsigned pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
     TcSmem &sm = *reinterpret_cast<TcSmem *>(raw + pad);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int z = blockIdx.y;
-    const long long row = (long long)blockIdx.x * TM + tid;
+    const long long row0 = (long long)blockIdx.x * TM;
+    // epilogue: warp w reads TMEM lane quadrant w % 4 (rows) and half w / 4 of the columns
+    const int quad = warp & 3, half = warp >> 2;
+    const int erow = quad * 32 + lane;
 
-    if (tid == 0) mbar_init(&sm.mbar, 1);
+    if (tid == 0) {
+        mbar_init(&sm.mbar, 1);
+        mbar_init(&sm.wbar, 1);
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(&sm.tmem)), "r"(TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // layer-0 operand: this thread's sample, BF16, zero-padded to kp[0] columns
-    {
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = sm.tmem;
+    if (tid == 0) load_layer(tc, sm, z, 0);
+    // layer-0 operand: one sample per thread of the first 128, BF16, zero-padded
+    if (tid < TM) {
+        const long long row = row0 + tid;
         const int k0 = tc.k[0], kp = tc.kp[0];
         for (int c = 0; c < kp; c += 8) {
             float v[8];
@@ -146,24 +179,17 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
             *reinterpret_cast<uint4 *>(sm.a + core_off(tid, c, kp)) = pack8(v);
         }
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     fence_before();
     __syncthreads();
-    fence_after();
-    const unsigned tmem = sm.tmem;
-    const unsigned lane_base = (unsigned)(warp * 32) << 16;
 
-    for (int l = 0; l < tc.L; l++) {
+    bool ok = true;
+    for (int l = 0; l < tc.L && ok; l++) {
         const int kp = tc.kp[l], np = tc.np[l];
         const bool last = l == tc.L - 1;
-        // the layer's weights (already in core-matrix layout) and bias
-        const uint4 *src = reinterpret_cast<const uint4 *>(tc.w + (long long)z * tc.wmember + tc.woff[l]);
-        uint4 *dst = reinterpret_cast<uint4 *>(sm.w);
-        const int n16 = np * kp / 8;
-        for (int i = tid; i < n16; i += NTH) dst[i] = src[i];
-        for (int i = tid; i < np; i += NTH) sm.bias[i] = tc.b[(long long)z * tc.bmember + tc.boff[l] + i];
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before();
-        __syncthreads();
+        // the layer's weights and bias have landed
+        ok = __syncthreads_and(mbar_wait(&sm.wbar, (unsigned)(l & 1)));
+        if (!ok) break;
         if (tid == 0) {
             fence_after();
             const unsigned a0 = smem_u32(sm.a), w0 = smem_u32(sm.w);
@@ -174,28 +200,27 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
                          id, kk > 0);
             mma_commit(&sm.mbar);
         }
-        const bool ok = mbar_wait(&sm.mbar, (unsigned)(l & 1));
-        if (!__syncthreads_and(ok)) {
-            // the products did not complete in time: count it, give them one more bounded
-            // wait, free TMEM below
-            if (tid == 0) {
-                atomicAdd(tc.err, 1u);
-                mbar_wait(&sm.mbar, (unsigned)(l & 1));
-            }
-            __syncthreads();
-            break;
-        }
+        ok = __syncthreads_and(mbar_wait(&sm.mbar, (unsigned)(l & 1)));
+        if (!ok) break;
         fence_after();
-        for (int c = 0; c < np; c += 16) {
+        // the products are done with the weight buffer: fetch the next layer's during the
+        // epilogue (its bias goes to the other bias buffer)
+        if (tid == 0 && !last) load_layer(tc, sm, z, l + 1);
+        const float *bias = sm.bias[l & 1];
+        const int chunks = np / 16, c0 = half ? (chunks + 1) / 2 : 0;
+        const int c1 = half ? chunks : (chunks + 1) / 2;
+        const long long row = row0 + erow;
+        for (int ch = c0; ch < c1; ch++) {
+            const int c = ch * 16;
             float v[16];
-            tmem_ld16(tmem + lane_base + (unsigned)c, v);
+            tmem_ld16(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)c, v);
 #pragma unroll
-            for (int j = 0; j < 16; j++) v[j] += sm.bias[c + j];
+            for (int j = 0; j < 16; j++) v[j] += bias[c + j];
             if (!last) {
 #pragma unroll
-                for (int j = 0; j < 16; j++) v[j] = gelu(v[j]);
-                *reinterpret_cast<uint4 *>(sm.a + core_off(tid, c, np)) = pack8(v);
-                *reinterpret_cast<uint4 *>(sm.a + core_off(tid, c + 8, np)) = pack8(v + 8);
+                for (int j = 0; j < 16; j++) v[j] = gelu_approx(v[j]);
+                *reinterpret_cast<uint4 *>(sm.a + core_off(erow, c, np)) = pack8(v);
+                *reinterpret_cast<uint4 *>(sm.a + core_off(erow, c + 8, np)) = pack8(v + 8);
             } else if (row < n) {
                 const int nout = tc.n[l];
 #pragma unroll
@@ -203,9 +228,23 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
                     if (c + j < nout) Y[((long long)z * n + row) * nout + c + j] = v[j];
             }
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         fence_before();
         __syncthreads();
     }
+    if (!ok) {
+        // a wait gave up: count it, give the copies and products in flight one more bounded
+        // wait, free TMEM below
+        if (tid == 0) {
+            atomicAdd(tc.err, 1u);
+            mbar_wait(&sm.wbar, 0);
+            mbar_wait(&sm.wbar, 1);
+            mbar_wait(&sm.mbar, 0);
+            mbar_wait(&sm.mbar, 1);
+        }
+        __syncthreads();
+    }
+    fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS) : "memory");
