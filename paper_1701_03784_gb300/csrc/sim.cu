@@ -108,7 +108,8 @@ struct SimImpl final : SimBase {
     double *dgl_ref = nullptr, *diag_out = nullptr;
 
     bool timing_on = false;
-    // host round trips (step_host): downloads run on their own stream, chunk by chunk
+    // host round trips (step_host): uploads and downloads run on streams of their own,
+    // chunk by chunk
     static constexpr int RT_CHUNKS = 8;
     // CUDA-graph replay of whole periods of steps (2 x the re-sort interval: the buffer
     // parities and the re-sort phase are back where they started)
@@ -120,8 +121,8 @@ struct SimImpl final : SimBase {
     cudaGraphExec_t g_exec = nullptr;
     int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1;
     int64_t g_bound = -1;
-    cudaStream_t rt_stream = nullptr;
-    cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr;
+    cudaStream_t rt_stream = nullptr, up_stream = nullptr;
+    cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr, rt_up = nullptr;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
 
@@ -134,7 +135,9 @@ struct SimImpl final : SimBase {
             for (auto e : rt_chunk) cudaEventDestroy(e);
             cudaEventDestroy(rt_step);
             cudaEventDestroy(rt_done);
+            cudaEventDestroy(rt_up);
             cudaStreamDestroy(rt_stream);
+            cudaStreamDestroy(up_stream);
         }
         for (auto &e : ev_pending) {
             cudaEventDestroy(e.first);
@@ -943,6 +946,8 @@ struct SimImpl final : SimBase {
         }
         if (!rt_stream) {
             PIC_CUDA_TRY(cudaStreamCreateWithFlags(&rt_stream, cudaStreamNonBlocking));
+            PIC_CUDA_TRY(cudaStreamCreateWithFlags(&up_stream, cudaStreamNonBlocking));
+            PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_up, cudaEventDisableTiming));
             for (auto &e : rt_chunk) PIC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_step, cudaEventDisableTiming));
             PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_done, cudaEventDisableTiming));
@@ -950,14 +955,20 @@ struct SimImpl final : SimBase {
         char *h = static_cast<char *>(state);
         const int64_t chunk = (n + RT_CHUNKS - 1) / RT_CHUNKS;
         pic_status st;
+        // uploads on their own stream, after the caller's earlier work
+        PIC_CUDA_TRY(cudaEventRecord(rt_up, s));
+        PIC_CUDA_TRY(cudaStreamWaitEvent(up_stream, rt_up, 0));
         for (int64_t k = 0; k < steps; k++) {
             // upload; chunk c waits only for the previous step's download of chunk c, so the
             // two copy directions overlap
             for (int c = 0; c < RT_CHUNKS; c++) {
                 const int64_t c0 = std::min(n, c * chunk), c1 = std::min(n, c0 + chunk);
-                if (k > 0) PIC_CUDA_TRY(cudaStreamWaitEvent(s, rt_chunk[c], 0));
-                if (c1 > c0 && (st = copy_slots(h, n, c0, c1, true, s)) != PIC_OK) return st;
+                if (k > 0) PIC_CUDA_TRY(cudaStreamWaitEvent(up_stream, rt_chunk[c], 0));
+                if (c1 > c0 && (st = copy_slots(h, n, c0, c1, true, up_stream)) != PIC_OK)
+                    return st;
             }
+            PIC_CUDA_TRY(cudaEventRecord(rt_up, up_stream));
+            PIC_CUDA_TRY(cudaStreamWaitEvent(s, rt_up, 0));
             if (k == 0) {
                 // the caller's state: its slot count, and a new Gauss-law reference
                 PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(int64_t), cudaMemcpyHostToDevice, s));
