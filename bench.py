@@ -124,7 +124,7 @@ class OracleSample:
     a bounded sample of the same workload: the same mesh, fields and step, the first
     n_sample beam particles."""
 
-    def __init__(self, wl, n_sample=CPU_SAMPLE):
+    def __init__(self, wl, n_sample=CPU_SAMPLE, pusher="boris"):
         from oracle.operators import Mesh
         from oracle import particles as OP
         import workloads as W
@@ -144,6 +144,7 @@ class OracleSample:
         self.n = n_sample
         self.n_edges = m.N1
         self.q_src = wl["weight"] * QE / (2 * math.pi)
+        self.pusher = OP.VAY if pusher == "vay" else OP.BORIS
 
     def step(self):
         """One particle step of the sample; returns (wall time in seconds, particles
@@ -153,12 +154,13 @@ class OracleSample:
         self.J[:] = 0
         self.Q[:] = 0
         self.OP.push(self.pm, self.E, self.Bavg, self.wl["bz"], self.wl["dt"], QE / ME, C0,
-                     self.q_src, self.tri, self.lam, self.u, self.J, self.Q, self.Qa)
+                     self.q_src, self.tri, self.lam, self.u, self.J, self.Q, self.Qa,
+                     pusher=self.pusher)
         return time.perf_counter() - t0, live
 
 
-def cpu_baseline(wl, budget_s=15.0):
-    s = OracleSample(wl)
+def cpu_baseline(wl, budget_s=15.0, pusher="boris"):
+    s = OracleSample(wl, pusher=pusher)
     done, el, pushed = 0, 0.0, 0
     while el < budget_s:
         dt_s, n = s.step()
@@ -168,8 +170,8 @@ def cpu_baseline(wl, budget_s=15.0):
     live = int(np.count_nonzero(s.tri >= 0))
     return {"value": pushed / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": "%d of %d beam particles, %d steps, same mesh, fields and dt; FP64 C "
-                      "oracle particle loop (gather, Boris, walk, scatter), single thread; %d "
-                      "live at end" % (s.n, len(wl["z"]), done, live)}
+                      "oracle particle loop (gather, %s, walk, scatter), single thread; %d "
+                      "live at end" % (s.n, len(wl["z"]), done, pusher.capitalize(), live)}
 
 
 def reduce_over_ranks(ms, e2e_ms, n_particles, n_slots, dist=None, device="cpu"):
@@ -189,7 +191,7 @@ def run_config(args, n_tris, n_edges, dt):
     return {"workload": "single BWO (rippled SWS, 12 periods), %d triangles, %d particles, "
                         "FP32 + int64 fixed-point J/Q" % (n_tris, args.particles),
             "n_tris": n_tris, "n_edges": n_edges, "particles": args.particles, "dt_s": dt,
-            "sort_interval": args.sort_interval,
+            "sort_interval": args.sort_interval, "pusher": args.pusher,
             "l2": "inputs larger than L2 (particle state %d MB)" % (args.particles * 24 // 2 ** 20),
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -200,7 +202,7 @@ def run_reference(args):
         return 0
     wl = workload(args.particles)
     wl["dt"] = args.dt or DT_BWO
-    s = OracleSample(wl)
+    s = OracleSample(wl, pusher=args.pusher)
     t, pushed = 0.0, 0
     for i in range(args.warmup + args.steps):
         el, n = s.step()
@@ -451,6 +453,8 @@ def main():
     ap.add_argument("--particles", type=int, default=16_000_000)
     ap.add_argument("--sort-interval", type=int, default=16)
     ap.add_argument("--dt", type=float, default=None)
+    ap.add_argument("--pusher", default="boris", choices=["boris", "vay"],
+                    help="velocity update of Eq. DLE (both arms)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", type=int, default=0,
@@ -498,6 +502,8 @@ def main():
     info = pic.pic_mesh_info(mesh)
     sim = pic.pic_sim_create(mesh, dt, wl["bz"], args.particles + 1024)
     pic.pic_sim_set_sort_interval(sim, args.sort_interval)
+    if args.pusher == "vay":
+        pic.pic_sim_set_pusher(sim, pic.PIC_PUSHER_VAY)
     import workloads as W
     E0 = bwo_edge_field(info["n_edges"], wl["e_scale"], 7 + rank)
     pic.pic_fields_set(sim, E0, np.zeros(info["n_tris"]))
@@ -582,7 +588,7 @@ def main():
                        "absorbed": diag["n_absorbed"]},
         }
         if not args.no_cpu_baseline:
-            cb = cpu_baseline(wl)
+            cb = cpu_baseline(wl, pusher=args.pusher)
             cb.pop("seconds", None)
             line["cpu_baseline"] = cb
         print(json.dumps(line))

@@ -159,11 +159,23 @@ pic_status pic_sim_create(pic_mesh *m, double dt, double bz_guide, int64_t max_p
 /* Steps between particle re-sorts by triangle (default 16; 0 disables re-sorting). */
 pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
 
+/* Velocity update of Eq. DLE (Sec. 3.3 adopts a corrected Boris scheme, citing Vay 2008).
+ * PIC_PUSHER_BORIS (default): half electric kick, rotation by the angle of
+ * t = q dt B / (2 m gamma(u-)), half electric kick; the magnetic term of Eq. DLE then
+ * uses the mean of u^{n-1/2} and u^{n+1/2} with one gamma.  PIC_PUSHER_VAY: the magnetic
+ * term uses the mean of the velocities v^{n-1/2} and v^{n+1/2}, and Eq. DLE is solved for
+ * u^{n+1/2} in closed form (gamma^{n+1/2} from a quadratic in gamma^2), which keeps a
+ * particle in crossed fields with E + v x B = 0 unaccelerated.  Both build precisions.
+ * Errors: ARG (null handle or unknown pusher). */
+enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
+pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher);
+
 /* Replay steps from a CUDA graph (off by default).  pic_step then records one period of
  * 2 x the re-sort interval steps (2 with re-sorting off) on an internal stream the first
  * time it is needed, and launches that graph on the caller's stream for every whole period
  * that starts at the recorded phase; other steps run as before.  Results are those of plain
- * steps.  The graph is recorded again after the slot bound or the re-sort interval changed;
+ * steps.  The graph is recorded again after the slot bound, the re-sort interval, the
+ * launch shapes or the pusher changed;
  * per-launch timing (pic_kernel_timing) bypasses it.  Not an operation of the paper: it
  * removes the host launch cost of small meshes. */
 pic_status pic_sim_set_graph(pic_sim *s, int32_t enable);
@@ -209,7 +221,8 @@ pic_status pic_step(pic_sim *s, int64_t n_steps, void *cuda_stream);
 
 /* Synchronous diagnostics (Sec. 3.5, Sec. 5.1.1) and optional field read-back:
  * E_out (N1), B_out (N2, B^{n-1/2}), J_out (N1, J^{n-1/2} of the last step in physical
- * units), each may be NULL. */
+ * units), each may be NULL.  out may be NULL too: no reductions run, only the requested
+ * arrays are copied (a plain field read-back). */
 pic_status pic_diagnostics(pic_sim *s, pic_diag *out, double *E_out, double *B_out,
                            double *J_out, void *cuda_stream);
 

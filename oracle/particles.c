@@ -1,6 +1,7 @@
 /*
- * FP64 oracle of one particle step: gather, relativistic Boris push, move with
- * rotate-back to the meridian plane, triangle walk, charge-conserving scatter.
+ * FP64 oracle of one particle step: gather, relativistic push (Boris, or Vay's
+ * correction of it), move with rotate-back to the meridian plane, triangle walk,
+ * charge-conserving scatter.
  *
  * TEST INFRASTRUCTURE ONLY: plain, slow reference code used to check the GPU library.
  * Shares no code with it.  Compiled with -ffp-contract=off so that x86 and Arm
@@ -75,6 +76,70 @@ static void cross3(const double a[3], const double b[3], double o[3])
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+static double dot3(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* Eq. DLE solved with Boris's splitting (Sec. 3.3): half electric kick, rotation about B
+ * by the angle of t = h B / gamma(u-), half electric kick.  h = q dt / (2 m). */
+static void kick_boris(const double u[3], const double Ef[3], const double Bf[3], double h,
+                       double c, double out[3])
+{
+    double um[3], tv[3], sv[3], c1[3], upr[3];
+    for (int i = 0; i < 3; i++) um[i] = u[i] + h * Ef[i];
+    double gam = sqrt(1.0 + dot3(um, um) / (c * c));
+    for (int i = 0; i < 3; i++) tv[i] = h * Bf[i] / gam;
+    double t2 = dot3(tv, tv);
+    for (int i = 0; i < 3; i++) sv[i] = 2.0 * tv[i] / (1.0 + t2);
+    cross3(um, tv, c1);
+    for (int i = 0; i < 3; i++) upr[i] = um[i] + c1[i];
+    cross3(upr, sv, c1);
+    for (int i = 0; i < 3; i++) out[i] = um[i] + c1[i] + h * Ef[i];
+}
+
+/* Eq. DLE with the velocity term read as the mean of v^{n-1/2} and v^{n+1/2} (Vay 2008,
+ * the correction the paper cites in Sec. 3.3), solved exactly:
+ *   u' = u + 2h E + h v x B,  v = u / gamma(u);  tau = h B;
+ *   gamma_new^2 is the positive root of g^4 - sigma g^2 - (tau^2 + (u'.tau / c)^2) = 0,
+ *   sigma = gamma(u')^2 - tau^2;  t = tau / gamma_new;
+ *   u_new = (u' + (u'.t) t + u' x t) / (1 + t^2). */
+static void kick_vay(const double u[3], const double Ef[3], const double Bf[3], double h,
+                     double c, double out[3])
+{
+    double v[3], vxb[3], up[3], tau[3], tv[3], c1[3];
+    double gam = sqrt(1.0 + dot3(u, u) / (c * c));
+    for (int i = 0; i < 3; i++) v[i] = u[i] / gam;
+    cross3(v, Bf, vxb);
+    for (int i = 0; i < 3; i++) up[i] = u[i] + 2.0 * h * Ef[i] + h * vxb[i];
+    for (int i = 0; i < 3; i++) tau[i] = h * Bf[i];
+    double tau2 = dot3(tau, tau);
+    double ustar = dot3(up, tau) / c;
+    double sigma = 1.0 + dot3(up, up) / (c * c) - tau2;
+    double gnew = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (tau2 + ustar * ustar))));
+    for (int i = 0; i < 3; i++) tv[i] = tau[i] / gnew;
+    double ut = dot3(up, tv);
+    double s = 1.0 / (1.0 + dot3(tv, tv));
+    cross3(up, tv, c1);
+    for (int i = 0; i < 3; i++) out[i] = s * (up[i] + ut * tv[i] + c1[i]);
+}
+
+static void kick(int pusher, const double u[3], const double Ef[3], const double Bf[3],
+                 double h, double c, double out[3])
+{
+    if (pusher == 1) kick_vay(u, Ef, Bf, h, c, out);
+    else kick_boris(u, Ef, Bf, h, c, out);
+}
+
+/* The velocity update alone, for n particles with given fields (rows of 3, local
+ * (rho, phi, z) components): pins of the two pushers. */
+int oracle_kick(int pusher, int64_t n, const double *u, const double *Ef, const double *Bf,
+                double h, double c, double *out)
+{
+    for (int64_t p = 0; p < n; p++) kick(pusher, u + 3 * p, Ef + 3 * p, Bf + 3 * p, h, c, out + 3 * p);
+    return 0;
+}
+
 /*
  * Push all particles one step.  On entry: tri/lam at step n, u at n-1/2; E at n,
  * Bavg = (B^{n+1/2} + B^{n-1/2}) / 2 per face.  On exit: tri/lam at n+1 (tri = -1 for
@@ -86,9 +151,9 @@ static void cross3(const double a[3], const double b[3], double o[3])
 int oracle_push(const int32_t *tri_nodes, const int32_t *tri_edges, const int32_t *tri_nbr,
                 const int32_t *tri_btag, const double *node_zr, const double *grad,
                 const double *area, const double *E, const double *Bavg, double bz,
-                double dt, double qm, double c, double q_src, int max_cross, int64_t np,
-                int32_t *tri, double *lam, double *u, double *J, double *Q, double *Qabs,
-                int64_t *counters)
+                double dt, double qm, double c, double q_src, int max_cross, int pusher,
+                int64_t np, int32_t *tri, double *lam, double *u, double *J, double *Q,
+                double *Qabs, int64_t *counters)
 {
     omesh m = {tri_nodes, tri_edges, tri_nbr, tri_btag, node_zr, grad, area};
     const double h = 0.5 * qm * dt;
@@ -105,19 +170,9 @@ int oracle_push(const int32_t *tri_nodes, const int32_t *tri_edges, const int32_
         double Ef[3] = {Er, 0.0, Ez};
         double Bf[3] = {0.0, Bavg[t] / area[t], bz};
 
-        /* relativistic Boris (Eq. DLE): half kick, rotation, half kick */
-        double um[3], up[3], tv[3], sv[3], c1[3];
-        for (int i = 0; i < 3; i++) um[i] = u[3 * p + i] + h * Ef[i];
-        double g2 = 1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) / (c * c);
-        double gam = sqrt(g2);
-        for (int i = 0; i < 3; i++) tv[i] = h * Bf[i] / gam;
-        double t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-        for (int i = 0; i < 3; i++) sv[i] = 2.0 * tv[i] / (1.0 + t2);
-        cross3(um, tv, c1);
-        double upr[3];
-        for (int i = 0; i < 3; i++) upr[i] = um[i] + c1[i];
-        cross3(upr, sv, c1);
-        for (int i = 0; i < 3; i++) up[i] = um[i] + c1[i] + h * Ef[i];
+        /* relativistic push (Eq. DLE) */
+        double up[3];
+        kick(pusher, u + 3 * p, Ef, Bf, h, c, up);
 
         /* move (Eq. DNE) in the Cartesian frame of the particle's azimuth, then rotate
          * back to the meridian plane */

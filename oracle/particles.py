@@ -12,6 +12,7 @@ _LIB = os.path.join(_HERE, "_liboracle.so")
 _lib = None
 
 WALK_CAP = 16   # edge crossings per particle per step before it is dropped
+BORIS, VAY = 0, 1   # velocity update of Eq. DLE (Sec. 3.3)
 
 
 def build_oracle_lib(force=False):
@@ -31,8 +32,10 @@ def _load():
         P = ctypes.c_void_p
         _lib.oracle_push.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_int, ctypes.c_int64,
-                                     P, P, P, P, P, P, P]
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int64, P, P, P, P, P, P, P]
+        _lib.oracle_kick.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, ctypes.c_double,
+                                     ctypes.c_double, P]
         _lib.oracle_deposit_charge.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double, P]
     return _lib
 
@@ -54,7 +57,21 @@ class PushMesh:
         self.area = np.ascontiguousarray(mesh.area, np.float64)
 
 
-def push(pm, E, Bavg, bz, dt, qm, c, q_src, tri, lam, u, J, Q, Qabs, max_cross=WALK_CAP):
+def kick(pusher, u, Ef, Bf, h, c):
+    """The velocity update of Eq. DLE alone (BORIS or VAY) for rows of u, E and B in local
+    (rho, phi, z) components; h = q dt / (2 m)."""
+    lib = _load()
+    u = np.ascontiguousarray(np.atleast_2d(u), np.float64)
+    Ef = np.ascontiguousarray(np.broadcast_to(Ef, u.shape), np.float64)
+    Bf = np.ascontiguousarray(np.broadcast_to(Bf, u.shape), np.float64)
+    out = np.zeros_like(u)
+    lib.oracle_kick(int(pusher), len(u), _ptr(u), _ptr(Ef), _ptr(Bf), float(h), float(c),
+                    _ptr(out))
+    return out
+
+
+def push(pm, E, Bavg, bz, dt, qm, c, q_src, tri, lam, u, J, Q, Qabs, max_cross=WALK_CAP,
+         pusher=BORIS):
     """One particle step in place (see oracle_push in particles.c).  Returns counters
     (absorbed, walk-cap overflows, edge crossings)."""
     lib = _load()
@@ -67,7 +84,7 @@ def push(pm, E, Bavg, bz, dt, qm, c, q_src, tri, lam, u, J, Q, Qabs, max_cross=W
     lib.oracle_push(_ptr(pm.tri_nodes), _ptr(pm.tri_edges), _ptr(pm.tri_nbr), _ptr(pm.tri_btag),
                     _ptr(pm.node_zr), _ptr(pm.grad), _ptr(pm.area), _ptr(E), _ptr(Bavg),
                     float(bz), float(dt), float(qm), float(c), float(q_src), int(max_cross),
-                    int(len(tri)), _ptr(tri), _ptr(lam), _ptr(u), _ptr(J), _ptr(Q), _ptr(Qabs),
+                    int(pusher), int(len(tri)), _ptr(tri), _ptr(lam), _ptr(u), _ptr(J), _ptr(Q), _ptr(Qabs),
                     _ptr(cnt))
     return cnt
 

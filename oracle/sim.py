@@ -3,7 +3,7 @@
 State at the start of step n: E^n (edges), B^{n-1/2} (faces), particle positions r^n
 (triangle + barycentric lambda), momenta u^{n-1/2}, node charges Q^n.
   1. B^{n+1/2} = B^{n-1/2} - dt D_curl E^n                        (Eq. full_d_dfl)
-  2. gather E^n and (B^{n+1/2} + B^{n-1/2})/2 at r^n, Boris push, walk, scatter
+  2. gather E^n and (B^{n+1/2} + B^{n-1/2})/2 at r^n, push (Boris or Vay), walk, scatter
      J^{n+1/2} (Eq. current) and Q^{n+1} (Eq. charge)              (Secs. 3.2-3.4)
   3. E^{n+1} = E^n + dt M (D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}) (Eq. full_d_dal)
 The auxiliary dual flux D^{n+1} = D^n + dt (D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}) is
@@ -44,6 +44,7 @@ class OracleSim:
         self.q = self.mass = self.weight = 0.0
         self.dt = None
         self.bz = 0.0
+        self.pusher = P.BORIS   # velocity update of Eq. DLE: P.BORIS or P.VAY
         self.counters = np.zeros(3, np.int64)
         self.n = 0
 
@@ -87,7 +88,7 @@ class OracleSim:
         Qn = np.zeros(m.N0)
         self.Qabs = np.zeros(m.N0)
         cnt = P.push(self.pm, self.E, Bavg, self.bz, self.dt, self.qm, self.c, self.q_src,
-                     self.tri, self.lam, self.u, self.J, Qn, self.Qabs)
+                     self.tri, self.lam, self.u, self.J, Qn, self.Qabs, pusher=self.pusher)
         self.counters += cnt
         return Qn
 

@@ -1,5 +1,6 @@
 // K5: diagnostics (Sec. 3.5, Sec. 5.1.1) as FP64 reductions on the device, and read-back
 // conversions.  Not on the per-step path.
+#include <algorithm>
 #include <type_traits>
 
 #include "pic_internal.h"
@@ -114,20 +115,37 @@ __global__ void __launch_bounds__(256) k_diag_energy(DiagDev d, const typename P
     if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out + 5, s);
 }
 
+// sum of (gamma - 1) over live particles; the FP32 build evaluates each term in FP32 (its
+// momenta are FP32) and sums in FP64.  Grid-stride, one atomic per block.
 template <class P>
 __global__ void __launch_bounds__(256) k_diag_kinetic(Particles<P> p, const int64_t *n_slots,
                                                       double inv_c2, double *out) {
-    int64_t n = *n_slots;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double part[8];
+    const int64_t n = *n_slots;
     double s = 0;
-    if (i < n && p.tri[i] >= 0) {
-        double u2 = (double)p.ur[i] * p.ur[i] + (double)p.up[i] * p.up[i] + (double)p.uz[i] * p.uz[i];
-        double g = sqrt(1.0 + u2 * inv_c2);
-        // (gamma - 1) without cancellation
-        s = u2 * inv_c2 / (g + 1.0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (p.tri[i] < 0) continue;
+        if constexpr (P::fixed) {
+            const float ic2 = (float)inv_c2;
+            const float ur = p.ur[i], up = p.up[i], uz = p.uz[i];
+            const float x = (ur * ur + up * up + uz * uz) * ic2;
+            // (gamma - 1) without cancellation
+            s += (double)(x / (sqrtf(1.f + x) + 1.f));
+        } else {
+            const double x = ((double)p.ur[i] * p.ur[i] + (double)p.up[i] * p.up[i] +
+                              (double)p.uz[i] * p.uz[i]) * inv_c2;
+            s += x / (sqrt(1.0 + x) + 1.0);
+        }
     }
     s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out + 6, s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0 && s != 0.0) atomicAdd(out + 6, s);
+    }
 }
 
 template <class P>
@@ -142,8 +160,10 @@ void launch_diag(const DiagDev &d, const typename P::Acc *J, const typename P::A
     if (set_ref) return;
     int64_t ne = d.N1 > d.N2 ? d.N1 : d.N2;
     k_diag_energy<P><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(d, E, B, mu_inv, out);
-    if (n_bound > 0)
-        k_diag_kinetic<P><<<(unsigned)((n_bound + 255) / 256), 256, 0, s>>>(p, n_slots, inv_c2, out);
+    if (n_bound > 0) {
+        const int64_t blocks = std::min<int64_t>((n_bound + 255) / 256, 1216);
+        k_diag_kinetic<P><<<(unsigned)blocks, 256, 0, s>>>(p, n_slots, inv_c2, out);
+    }
 }
 
 template <class P>

@@ -31,6 +31,36 @@ __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 
+// Eq. DLE with its magnetic term read as the mean of the velocities v^{n-1/2} and
+// v^{n+1/2} (Vay 2008, the correction cited in Sec. 3.3), solved in closed form.  Fields in
+// the local frame: E = (Er, 0, Ez), B = (0, bphi, bz); h = q dt / (2 m).
+//   u' = u + 2h E + h (u / gamma(u)) x B,  tau = h B,
+//   gamma_new^2 = (sigma + sqrt(sigma^2 + 4 (tau^2 + (u'.tau)^2 / c^2))) / 2,
+//   sigma = gamma(u')^2 - tau^2 (the other form of the root when sigma < 0),
+//   t = tau / gamma_new,  u_new = (u' + (u'.t) t + u' x t) / (1 + t^2).
+template <class R>
+__device__ __forceinline__ Vec3<R> kick_vay(const Vec3<R> &u, R Er, R Ez, R bphi, R bz, R h,
+                                            R inv_c2) {
+    const R gi = rsqrt_(R(1) + (u.r * u.r + u.p * u.p + u.z * u.z) * inv_c2);
+    const R tp = h * bphi, tz = h * bz;
+    const R hg = gi;
+    // (u / gamma) x tau with tau = (0, tp, tz)
+    const Vec3<R> p = {u.r + R(2) * h * Er + hg * (u.p * tz - u.z * tp), u.p - hg * u.r * tz,
+                       u.z + R(2) * h * Ez + hg * u.r * tp};
+    const R tau2 = tp * tp + tz * tz;
+    const R ut0 = p.p * tp + p.z * tz;
+    const R x = tau2 + ut0 * ut0 * inv_c2;
+    const R sigma = R(1) + (p.r * p.r + p.p * p.p + p.z * p.z) * inv_c2 - tau2;
+    const R disc = sqrt_(sigma * sigma + R(4) * x);
+    const R g2 = sigma >= R(0) ? R(0.5) * (sigma + disc) : R(2) * x / (disc - sigma);
+    const R gn = rsqrt_(g2);
+    const R qp = tp * gn, qz = tz * gn;
+    const R ut = p.p * qp + p.z * qz;
+    const R sf = R(1) / (R(1) + qp * qp + qz * qz);
+    return Vec3<R>{sf * (p.r + p.p * qz - p.z * qp), sf * (p.p + ut * qp - p.r * qz),
+                   sf * (p.z + ut * qz + p.r * qp)};
+}
+
 // barycentric state: FP32 keeps exact integers (units 2^-22, sum 2^22) plus their float
 // values; FP64 keeps doubles
 template <class P>
@@ -164,15 +194,22 @@ __global__ void __launch_bounds__(256) k_push(PushArgs<P> a) {
         R Er = l.f[0] * rc->c[1] + l.f[1] * rc->c[3] + l.f[2] * rc->c[5];
         R rho = l.f[0] * rc->rho[0] + l.f[1] * rc->rho[1] + l.f[2] * rc->rho[2];
         const R h = a.qmdt2;
-        // relativistic Boris (Eq. DLE)
-        Vec3<R> um = {a.p.ur[i] + h * Er, a.p.up[i], a.p.uz[i] + h * Ez};
-        R g_inv = rsqrt_(R(1) + (um.r * um.r + um.p * um.p + um.z * um.z) * a.inv_c2);
-        Vec3<R> tv = {R(0), h * rc->bphi * g_inv, h * a.bz * g_inv};
-        R sfac = R(2) / (R(1) + tv.p * tv.p + tv.z * tv.z);
-        Vec3<R> c1 = cross(um, tv);
-        Vec3<R> upr = {um.r + c1.r, um.p + c1.p, um.z + c1.z};
-        Vec3<R> c2 = cross(upr, Vec3<R>{R(0), sfac * tv.p, sfac * tv.z});
-        Vec3<R> u = {um.r + c2.r + h * Er, um.p + c2.p, um.z + c2.z + h * Ez};
+        // relativistic push (Eq. DLE)
+        Vec3<R> u;
+        if (a.pusher == PIC_PUSHER_VAY) {
+            u = kick_vay<R>(Vec3<R>{a.p.ur[i], a.p.up[i], a.p.uz[i]}, Er, Ez, rc->bphi, a.bz, h,
+                            a.inv_c2);
+        } else {
+            // Boris: half kick, rotation by t = h B / gamma(u-), half kick
+            Vec3<R> um = {a.p.ur[i] + h * Er, a.p.up[i], a.p.uz[i] + h * Ez};
+            R g_inv = rsqrt_(R(1) + (um.r * um.r + um.p * um.p + um.z * um.z) * a.inv_c2);
+            Vec3<R> tv = {R(0), h * rc->bphi * g_inv, h * a.bz * g_inv};
+            R sfac = R(2) / (R(1) + tv.p * tv.p + tv.z * tv.z);
+            Vec3<R> c1 = cross(um, tv);
+            Vec3<R> upr = {um.r + c1.r, um.p + c1.p, um.z + c1.z};
+            Vec3<R> c2 = cross(upr, Vec3<R>{R(0), sfac * tv.p, sfac * tv.z});
+            u = Vec3<R>{um.r + c2.r + h * Er, um.p + c2.p, um.z + c2.z + h * Ez};
+        }
         // move (Eq. DNE) in the ring's Cartesian frame, rotate back to the meridian plane
         R gn_inv = rsqrt_(R(1) + (u.r * u.r + u.p * u.p + u.z * u.z) * a.inv_c2);
         R xr = u.r * gn_inv * a.dt, yp = u.p * gn_inv * a.dt;
@@ -375,20 +412,32 @@ void launch_push(const PushArgs<P> &a, int64_t n_bound, cudaStream_t s) {
     }
 }
 
-// charge of newly injected particles, slots [first, first + count)
+// Eq. charge of the particles in slots [first, first + count) (new particles at
+// injection; all of them for the diagnostics).  FP32 build: the fixed-point coordinates of
+// the lanes that share a triangle are summed first (sorted slots: most lanes of a warp do),
+// one set of atomics per triangle; sums of at most 32 coordinates < 2^23 fit in 32 bits.
 template <class P>
 __global__ void k_deposit_q(const TriRec<typename P::R> *rec, Particles<P> p, int64_t first,
                             int64_t count, typename P::Acc *Q) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= count) return;
-    int64_t i = first + k;
-    int t = p.tri[i];
-    if (t < 0) return;
-    Bary<P> l;
-    load_bary<P>(p, i, l);
-    for (int m = 0; m < 3; m++) {
-        if constexpr (P::fixed) atomic_acc(Q + rec[t].node[m], (long long)l.q[m]);
-        else atomic_acc(Q + rec[t].node[m], l.f[m]);
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = first + k;
+    const int t = k < count ? p.tri[i] : -1;
+    if constexpr (P::fixed) {
+        const unsigned grp = __match_any_sync(0xffffffffu, t);
+        if (t < 0) return;
+        const unsigned a = (unsigned)p.l0[i], b = (unsigned)p.l1[i];
+        const unsigned sa = __reduce_add_sync(grp, a), sb = __reduce_add_sync(grp, b);
+        if ((threadIdx.x & 31) == __ffs(grp) - 1) {
+            const long long sc = (long long)__popc(grp) * LAM_ONE - (long long)sa - (long long)sb;
+            atomic_acc(Q + rec[t].node[0], (long long)sa);
+            atomic_acc(Q + rec[t].node[1], (long long)sb);
+            atomic_acc(Q + rec[t].node[2], sc);
+        }
+    } else {
+        if (t < 0) return;
+        Bary<P> l;
+        load_bary<P>(p, i, l);
+        for (int m = 0; m < 3; m++) atomic_acc(Q + rec[t].node[m], l.f[m]);
     }
 }
 

@@ -1,5 +1,6 @@
-// K1, FP32 build: fused particle step -- Whitney gather, relativistic Boris push,
-// rotate-back to the meridian plane, triangle walk, charge-conserving current scatter.
+// K1, FP32 build: fused particle step -- Whitney gather, relativistic push (Boris, or the
+// Vay form of Eq. DLE: one instantiation each), rotate-back to the meridian plane, triangle
+// walk, charge-conserving current scatter.
 //
 // Positions are fixed-point barycentric coordinates (integers in units of 2^-22 that sum
 // to 2^22).  Every segment's current lambda_a^s lambda_b^e - lambda_b^s lambda_a^e
@@ -13,7 +14,7 @@
 //  * one producer warp (lane 0) stages tiles of TILE slots (structure of arrays, sorted
 //    by triangle) into shared memory with 1-D bulk copies, STAGES buffers deep; a
 //    buffer is refilled once all compute warps have arrived on its "empty" mbarrier;
-//  * 8 compute warps advance two slots per thread per tile, branch-free: gather, Boris,
+//  * 8 compute warps advance two slots per thread per tile, branch-free: gather, push,
 //    rotate-back and the end point in the start triangle.  For the ~4 in 5 particles
 //    whose end point stays there, the edge currents are summed over the lanes that
 //    share the triangle (match.any, then redux.sync on two 23-bit limbs) and one lane
@@ -252,11 +253,12 @@ __device__ __forceinline__ void issue_tile(const PushArgs<PF32> &a, PushSmem &sm
     bulk_load(b.uz, a.p.uz + base, bytes, bar);
 }
 
-// Gather, Boris, rotate-back and the end of the move for one particle (slot i, state from
+// Gather, push, rotate-back and the end of the move for one particle (slot i, state from
 // the staged tile).  A particle whose end point stays in its start triangle t0 gets its
 // current as (A1, s0 - e0, s1 - e1) (see ccw_from) and its new position stored; one that
 // leaves t0 is described in e, flagged, and contributes no current here (its whole path,
 // the part in t0 included, is walked later).
+template <bool VAY>
 __device__ __forceinline__ void push_particle(const PushArgs<PF32> &a, int i, int t0, int s0,
                                               int s1, float ur, float up, float uz,
                                               long long &a1, int &dq0, int &dq1, int &flags,
@@ -273,21 +275,47 @@ __device__ __forceinline__ void push_particle(const PushArgs<PF32> &a, int i, in
     const float rho = f0 * RH.x + f1 * RH.y + f2 * RH.z;
     const float h = a.qmdt2;
 
-    // relativistic Boris (Eq. DLE): half kick, rotation about B = (0, B_phi, B_z), half kick
-    ur += h * Er;
-    uz += h * Ez;
-    float gi = rsqrtf(1.f + (ur * ur + up * up + uz * uz) * a.inv_c2);
-    const float tp = h * CB.z * gi, tz = h * a.bz * gi;
-    const float sf = __fdividef(2.f, 1.f + tp * tp + tz * tz);
-    const float pr = ur + (up * tz - uz * tp);   // u' = u- + u- x t, t = (0, tp, tz)
-    const float pp = up - ur * tz;
-    const float pz = uz + ur * tp;
-    ur += sf * (pp * tz - pz * tp) + h * Er;      // u+ = u- + u' x (sf t), then half kick
-    up -= sf * pr * tz;
-    uz += sf * pr * tp + h * Ez;
+    if constexpr (VAY) {
+        // Eq. DLE with the mean of v^{n-1/2} and v^{n+1/2} in the magnetic term (Vay),
+        // solved in closed form: u' = u + 2h E + h (u / gamma) x B, tau = h B, gamma_new^2
+        // the positive root of g^4 - sigma g^2 - (tau^2 + (u'.tau)^2 / c^2),
+        // t = tau / gamma_new, u = (u' + (u'.t) t + u' x t) / (1 + t^2)
+        const float gi = rsqrtf(1.f + (ur * ur + up * up + uz * uz) * a.inv_c2);
+        const float tp = h * CB.z, tz = h * a.bz;
+        const float pr = ur + 2.f * h * Er + gi * (up * tz - uz * tp);
+        const float pp = up - gi * ur * tz;
+        const float pz = uz + 2.f * h * Ez + gi * ur * tp;
+        const float tau2 = tp * tp + tz * tz;
+        const float ut0 = pp * tp + pz * tz;
+        const float x = tau2 + ut0 * ut0 * a.inv_c2;
+        const float sigma = 1.f + (pr * pr + pp * pp + pz * pz) * a.inv_c2 - tau2;
+        const float disc = sqrtf(sigma * sigma + 4.f * x);
+        const float g2 = sigma >= 0.f ? 0.5f * (sigma + disc) : __fdividef(2.f * x, disc - sigma);
+        const float gn = rsqrtf(g2);
+        const float qp = tp * gn, qz = tz * gn;
+        const float ut = pp * qp + pz * qz;
+        const float sf = __fdividef(1.f, 1.f + qp * qp + qz * qz);
+        ur = sf * (pr + pp * qz - pz * qp);
+        up = sf * (pp + ut * qp - pr * qz);
+        uz = sf * (pz + ut * qz + pr * qp);
+    } else {
+        // relativistic Boris (Eq. DLE): half kick, rotation about B = (0, B_phi, B_z), half
+        // kick
+        ur += h * Er;
+        uz += h * Ez;
+        const float gi = rsqrtf(1.f + (ur * ur + up * up + uz * uz) * a.inv_c2);
+        const float tp = h * CB.z * gi, tz = h * a.bz * gi;
+        const float sf = __fdividef(2.f, 1.f + tp * tp + tz * tz);
+        const float pr = ur + (up * tz - uz * tp);   // u' = u- + u- x t, t = (0, tp, tz)
+        const float pp = up - ur * tz;
+        const float pz = uz + ur * tp;
+        ur += sf * (pp * tz - pz * tp) + h * Er;      // u+ = u- + u' x (sf t), then half kick
+        up -= sf * pr * tz;
+        uz += sf * pr * tp + h * Ez;
+    }
 
     // move (Eq. DNE) in the ring's Cartesian frame, rotate back to the meridian plane
-    gi = rsqrtf(1.f + (ur * ur + up * up + uz * uz) * a.inv_c2);
+    const float gi = rsqrtf(1.f + (ur * ur + up * up + uz * uz) * a.inv_c2);
     const float xr = ur * gi * a.dt, yp = up * gi * a.dt;
     const float x = rho + xr;
     const float rn2 = x * x + yp * yp;
@@ -432,6 +460,7 @@ __device__ __forceinline__ unsigned walk_pass(const PushArgs<PF32> &a, const QEn
 
 }  // namespace
 
+template <bool VAY>
 __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PushSmem &sm = *reinterpret_cast<PushSmem *>(smem_raw);
@@ -498,8 +527,8 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
                 bool crossed = false;
                 QEntry e;
                 if (t0 >= 0)
-                    push_particle(a, (int)i, t0, b.l0[k], b.l1[k], b.ur[k], b.up[k], b.uz[k], a1,
-                                  dq0, dq1, flags, crossed, e);
+                    push_particle<VAY>(a, (int)i, t0, b.l0[k], b.l1[k], b.ur[k], b.up[k], b.uz[k],
+                                       a1, dq0, dq1, flags, crossed, e);
                 // currents of the particles that stay: summed over the lanes of each start
                 // triangle (one 64-bit and two 32-bit sums determine all three edges), one
                 // set of atomics per triangle
@@ -545,18 +574,18 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
 struct LaunchShape {
     int bps = 0, sms = 0;
 };
-static LaunchShape g_push_shape[64];
+static LaunchShape g_push_shape[2][64];
 
-void launch_push_f32(const PushArgs<PF32> &a, int64_t n_bound, cudaStream_t s) {
-    if (n_bound <= 0) return;
+template <bool VAY>
+static void launch_push_f32_as(const PushArgs<PF32> &a, int64_t n_bound, cudaStream_t s) {
     const int smem = (int)sizeof(PushSmem);
     int dev = 0;
     cudaGetDevice(&dev);
-    LaunchShape &ps = g_push_shape[dev & 63];
+    LaunchShape &ps = g_push_shape[VAY ? 1 : 0][dev & 63];
     if (ps.bps == 0) {
-        cudaFuncSetAttribute(k_push_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_push_f32<VAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int bps = 0, sms = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_push_f32, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_push_f32<VAY>, NT, smem);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         ps.bps = bps > 0 ? bps : 1;
         ps.sms = sms > 0 ? sms : 1;
@@ -564,7 +593,13 @@ void launch_push_f32(const PushArgs<PF32> &a, int64_t n_bound, cudaStream_t s) {
     const int64_t tiles = (n_bound + TILE - 1) / TILE;
     const int bps = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, ps.bps) : ps.bps;
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)ps.sms * bps);
-    k_push_f32<<<(unsigned)grid, NT, smem, s>>>(a);
+    k_push_f32<VAY><<<(unsigned)grid, NT, smem, s>>>(a);
+}
+
+void launch_push_f32(const PushArgs<PF32> &a, int64_t n_bound, cudaStream_t s) {
+    if (n_bound <= 0) return;
+    if (a.pusher == PIC_PUSHER_VAY) launch_push_f32_as<true>(a, n_bound, s);
+    else launch_push_f32_as<false>(a, n_bound, s);
 }
 
 }  // namespace pic

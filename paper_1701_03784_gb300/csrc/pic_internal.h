@@ -208,6 +208,7 @@ struct PushArgs {
     typename P::R bz;
     int32_t walk_cap;
     int32_t ctas_per_sm;        // launch shape: persistent CTAs per SM (0: as many as fit)
+    int32_t pusher;             // PIC_PUSHER_BORIS or PIC_PUSHER_VAY (Eq. DLE)
 };
 
 template <class P>

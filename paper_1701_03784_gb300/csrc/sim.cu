@@ -72,6 +72,7 @@ struct SimBase {
     virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
     virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
     int32_t sort_interval = 16;
+    int32_t pusher = PIC_PUSHER_BORIS;
     int device = 0;
 };
 
@@ -119,7 +120,7 @@ struct SimImpl final : SimBase {
     int32_t tune_ctas = 0, tune_block = 256;
     cudaStream_t g_stream = nullptr;
     cudaGraphExec_t g_exec = nullptr;
-    int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1;
+    int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1, g_ctas = -1, g_block = -1, g_pusher = -1;
     int64_t g_bound = -1;
     cudaStream_t rt_stream = nullptr, up_stream = nullptr;
     cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr, rt_up = nullptr;
@@ -512,7 +513,9 @@ struct SimImpl final : SimBase {
                 done += k;
                 continue;
             }
-            if (g_exec && (g_bound != n_bound || g_interval != sort_interval)) {
+            // a graph records the launch shapes and the pusher with the buffers
+            if (g_exec && (g_bound != n_bound || g_interval != sort_interval || g_ctas != tune_ctas ||
+                           g_block != tune_block || g_pusher != pusher)) {
                 cudaGraphExecDestroy(g_exec);
                 g_exec = nullptr;
             }
@@ -600,6 +603,9 @@ struct SimImpl final : SimBase {
         g_since = since_sort;
         g_bound = n_bound;
         g_interval = sort_interval;
+        g_ctas = tune_ctas;
+        g_block = tune_block;
+        g_pusher = pusher;
         PIC_CUDA_TRY(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
         pic_status st = step_direct(L, g_stream);
         cudaGraph_t graph = nullptr;
@@ -654,6 +660,7 @@ struct SimImpl final : SimBase {
             pa.bz = (R)bz;
             pa.walk_cap = m->units.walk_cap;
             pa.ctas_per_sm = tune_ctas;
+            pa.pusher = pusher;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (timing_on) {
                 e0 = take_event();
@@ -1085,6 +1092,16 @@ extern "C" pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval) {
         return PIC_ERR_ARG;
     }
     s->impl->sort_interval = interval;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher) {
+    SIM_CHECK(s, "pic_sim_set_pusher");
+    if (pusher != PIC_PUSHER_BORIS && pusher != PIC_PUSHER_VAY) {
+        set_error("pic_sim_set_pusher: unknown pusher %d", (int)pusher);
+        return PIC_ERR_ARG;
+    }
+    s->impl->pusher = pusher;
     return PIC_OK;
 }
 

@@ -18,6 +18,7 @@ PIC_OK, PIC_ERR_ARG, PIC_ERR_MESH, PIC_ERR_CUDA, PIC_ERR_UNSTABLE, PIC_ERR_TIMEO
     PIC_ERR_OOM, PIC_ERR_STATE = range(8)
 PIC_BC_PEC, PIC_BC_AXIS, PIC_BC_ABSORB = 1, 2, 3
 PIC_FP64, PIC_FP32 = 0, 1
+PIC_PUSHER_BORIS, PIC_PUSHER_VAY = 0, 1
 _STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_MESH", 3: "PIC_ERR_CUDA",
            4: "PIC_ERR_UNSTABLE", 5: "PIC_ERR_TIMEOUT", 6: "PIC_ERR_OOM", 7: "PIC_ERR_STATE"}
 
@@ -62,6 +63,7 @@ _SIGS = {
     "pic_spai_get": [_P, _P, _P, _P, _P],
     "pic_sim_create": [_P, _D, _D, _I64, _P],
     "pic_sim_set_sort_interval": [_P, _I32],
+    "pic_sim_set_pusher": [_P, _I32],
     "pic_sim_set_graph": [_P, _I32],
     "pic_sim_autotune": [_P, _I32, _P, _P],
     "pic_mlp_create": [_I32, _I32, _P, _I32, _P],
@@ -272,6 +274,11 @@ def pic_sim_set_sort_interval(sim, interval):
     _check(_lib.pic_sim_set_sort_interval(sim.ptr, interval), "pic_sim_set_sort_interval")
 
 
+def pic_sim_set_pusher(sim, pusher):
+    """PIC_PUSHER_BORIS (default) or PIC_PUSHER_VAY: the velocity update of Eq. DLE."""
+    _check(_lib.pic_sim_set_pusher(sim.ptr, pusher), "pic_sim_set_pusher")
+
+
 def pic_sim_set_graph(sim, enable=True):
     _check(_lib.pic_sim_set_graph(sim.ptr, 1 if enable else 0), "pic_sim_set_graph")
 
@@ -324,6 +331,16 @@ def pic_diagnostics(sim, fields=False, stream=None):
     if fields:
         out.update(E=E, B=B, J=J)
     return out
+
+
+def pic_fields_get(sim, stream=None):
+    """(E on edges, B on faces) as float64 arrays: pic_diagnostics without its reductions."""
+    info = pic_mesh_info(sim.mesh)
+    E = np.zeros(info["n_edges"])
+    B = np.zeros(info["n_tris"])
+    _check(_lib.pic_diagnostics(sim.ptr, None, _ptr(E), _ptr(B), None, _stream(stream)),
+           "pic_diagnostics")
+    return E, B
 
 
 def pic_charges_get_static(sim, Q=None, Q_prev=None, Q_absorbed=None, stream=None):

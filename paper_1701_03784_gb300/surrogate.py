@@ -73,7 +73,7 @@ def batch_outputs(instances, dt, bz, steps, every, q, m, w, eps0, mu0, c, sort_i
     bprobe = np.zeros((n, samples))
     for s in range(samples):
         pic.pic_step(sim, every)
-        B = pic.pic_diagnostics(sim, fields=True)["B"]
+        B = pic.pic_fields_get(sim)[1]
         energy[:, s] = np.bincount(inst[out], weights=(coef * B * B)[out], minlength=n)
         bprobe[:, s] = B[probe]
     env = np.log10(energy.reshape(n, N_ENV, samples // N_ENV).mean(2) + 1e-300)

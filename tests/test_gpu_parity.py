@@ -45,7 +45,7 @@ def _copy(o):
 
 
 def _setup(pic, mesh_arrays, oracle, prec, n, seed, dt_frac=0.5, bz=0.3, sigma_u=0.3,
-           e_scale=0.05, walk_cap=0, sort_interval=4, cap=None):
+           e_scale=0.05, walk_cap=0, sort_interval=4, cap=None, pusher="boris"):
     nodes, tris, be, bt = mesh_arrays
     o = _copy(oracle)
     m = o.mesh
@@ -60,6 +60,9 @@ def _setup(pic, mesh_arrays, oracle, prec, n, seed, dt_frac=0.5, bz=0.3, sigma_u
     pic.pic_spai_build(mesh)
     sim = pic.pic_sim_create(mesh, dt, bz, cap or 2 * n + 16)
     pic.pic_sim_set_sort_interval(sim, sort_interval)
+    if pusher == "vay":
+        o.pusher = OP.VAY
+        pic.pic_sim_set_pusher(sim, pic.PIC_PUSHER_VAY)
     pic.pic_fields_set(sim, E0, B0)
     pic.pic_particles_inject(sim, z, r, ur, up, uz, -1.0, 1.0, 1e-3)
     if walk_cap:
@@ -90,7 +93,7 @@ def _oracle_step(o, n_steps, cap):
         Qn = np.zeros(m.N0)
         o.Qabs = np.zeros(m.N0)
         o.counters += OP.push(o.pm, o.E, Bavg, o.bz, o.dt, o.qm, o.c, o.q_src, o.tri, o.lam,
-                              o.u, o.J, Qn, o.Qabs, max_cross=cap)
+                              o.u, o.J, Qn, o.Qabs, max_cross=cap, pusher=o.pusher)
         o.field_e(B_half)
         o.B = B_half
         o.Q_prev, o.Q = o.Q, Qn
@@ -101,12 +104,13 @@ def _positions(nodes, tris, tri, lam):
     return np.einsum("nk,nkd->nd", lam, p)
 
 
+@pytest.mark.parametrize("pusher", ["boris", "vay"])
 @pytest.mark.parametrize("steps", [1, 5])
-def test_fp64_matches_oracle(pic, cavity_oracle, steps):
+def test_fp64_matches_oracle(pic, cavity_oracle, steps, pusher):
     """FP64 build: particle state, fields and scatter within 1e-12 of the oracle."""
     arrays, oracle = cavity_oracle
     n = 10_000
-    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP64, n, seed=10)
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP64, n, seed=10, pusher=pusher)
     pic.pic_step(sim, steps)
     _oracle_step(o, steps, cap)
     d = pic.pic_diagnostics(sim, fields=True)
@@ -126,13 +130,14 @@ def test_fp64_matches_oracle(pic, cavity_oracle, steps):
     assert d["dce_max"] < 1e-12 and d["dgl_drift"] < 1e-12
 
 
+@pytest.mark.parametrize("pusher", ["boris", "vay"])
 @pytest.mark.parametrize("steps", [1, 3])
-def test_fp32_matches_oracle(pic, cavity_oracle, steps):
+def test_fp32_matches_oracle(pic, cavity_oracle, steps, pusher):
     """FP32 build: 1e-5 relative per step; triangle ids equal except within 1e-5 of an edge."""
     arrays, oracle = cavity_oracle
     nodes, tris = arrays[0], arrays[1]
     n = 10_000
-    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, n, seed=20)
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, pic.PIC_FP32, n, seed=20, pusher=pusher)
     pic.pic_step(sim, steps)
     _oracle_step(o, steps, cap)
     d = pic.pic_diagnostics(sim, fields=True)
@@ -344,7 +349,8 @@ def test_step_host_matches_device_steps(pic, cavity_oracle, prec):
 def test_graph_replay_matches_plain_steps(pic, cavity_oracle):
     """pic_step replaying a CUDA graph of one period (re-sort every 3 steps: 6 steps) gives
     the state of plain steps, bit for bit in the FP32 build: 45 steps in calls of 1, 7, 13
-    and 24 steps, so that periods start at different phases and tails run plainly."""
+    and 24 steps, so that periods start at different phases and tails run plainly; then 12
+    more steps with the Vay pusher (the recorded graph must not be replayed for them)."""
     arrays, oracle = cavity_oracle
     runs = []
     for graph in (False, True):
@@ -353,12 +359,14 @@ def test_graph_replay_matches_plain_steps(pic, cavity_oracle):
         pic.pic_sim_set_graph(sim, graph)
         for k in (1, 7, 13, 24):
             pic.pic_step(sim, k)
+        pic.pic_sim_set_pusher(sim, pic.PIC_PUSHER_VAY)
+        pic.pic_step(sim, 12)
         d = pic.pic_diagnostics(sim, fields=True)
         g = pic.pic_particles_get(sim)
         order = np.argsort(g["pid"])
         runs.append(({k: g[k][order] for k in ("pid", "tri", "lam", "u")}, d))
     (g1, d1), (g2, d2) = runs
-    assert d1["n_steps"] == d2["n_steps"] == 45 and d1["n_absorbed"] > 0
+    assert d1["n_steps"] == d2["n_steps"] == 57 and d1["n_absorbed"] > 0
     for k in ("pid", "tri", "lam", "u"):
         assert np.array_equal(g1[k], g2[k]), k
     for k in ("E", "B", "J", "n_crossings", "n_absorbed", "dce_nonzero", "dgl_drift"):
@@ -393,3 +401,30 @@ def test_autotune_changes_no_result(pic, cavity_oracle):
         assert np.array_equal(g1[k], g2[k]), k
     for k in ("E", "B", "J", "n_crossings", "n_absorbed", "dce_nonzero"):
         assert np.array_equal(d1[k], d2[k]), k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_energy_diagnostics_match_the_oracle_definitions(pic, cavity_oracle, prec):
+    """The device reductions behind pic_diagnostics: the kinetic energy (sum over live
+    particles of (gamma - 1) m c^2 w) and the field energy (1/2 E star_eps E + 1/2 B
+    star_mu^-1 B) equal the oracle's definitions evaluated on the state read back."""
+    arrays, oracle = cavity_oracle
+    P = pic.PIC_FP64 if prec == "fp64" else pic.PIC_FP32
+    n = 30_000
+    o, sim, mesh, cap = _setup(pic, arrays, oracle, P, n, seed=70, sigma_u=0.8)
+    pic.pic_step(sim, 5)
+    d = pic.pic_diagnostics(sim, fields=True)
+    tri, lam, u = _gpu_particles(pic, sim, n)
+    assert (tri >= 0).sum() == d["n_particles"]
+    o.tri, o.u = tri, u
+    o.E, o.B = d["E"], d["B"]
+    # FP32 build: each (gamma - 1) term is evaluated in FP32, and the diagonal star_mu^-1
+    # is stored in FP32 (relative rounding 6e-8 per face)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert d["kinetic_energy"] == pytest.approx(o.kinetic_energy(), rel=tol)
+    assert d["field_energy"] == pytest.approx(o.field_energy(), rel=1e-12 if prec == "fp64" else 1e-7)
+    # the plain read-back (no reductions) returns the same fields
+    E, B = pic.pic_fields_get(sim)
+    assert np.array_equal(E, d["E"]) and np.array_equal(B, d["B"])
+    pic.pic_sim_destroy(sim)
+    pic.pic_mesh_destroy(mesh)
