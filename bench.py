@@ -444,6 +444,91 @@ def run_mlp_queries(args):
     return 0
 
 
+SPAI_SWEEP = [(1, 1e-4), (2, 1e-2), (2, 1e-4), (3, 1e-3), (3, 1e-4)]
+
+
+def _dominant_frequency(t, a, w_main, w_other):
+    """Least-squares fit of two sinusoids to a(t); the frequency of the larger one."""
+    from scipy.optimize import least_squares
+
+    def res(p):
+        return (p[0] * np.cos(p[2] * t) + p[1] * np.sin(p[2] * t)
+                + p[3] * np.cos(p[5] * t) + p[4] * np.sin(p[5] * t) - a)
+    p = least_squares(res, [a[0], 0.0, w_main, 0.0, 0.0, w_other], x_scale="jac").x
+    return p[2] if np.hypot(p[0], p[1]) > np.hypot(p[3], p[4]) else p[5]
+
+
+def run_spai_sweep(args):
+    """SPAI pattern level and drop tolerance (Sec. 3.1 gives neither) against accuracy and
+    cost.  Accuracy: the normalised cavity (c = 1, about 2000 triangles, FP64 build), TM010 +
+    TM011 line integrals as E^0, 1000 steps at half the stable step; the frequencies of the
+    two mode projections against the Bessel-zero closed form.  Cost: the BWO mesh (FP32
+    build, no particles), the three field kernels per step, CUDA events over 2000 steps."""
+    import torch
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import pic
+    import workloads as W
+    cav = W.cavity_mesh()
+    wl = workload(1024)
+    w010, w011 = W.tm0np_omega(0.5, 1.0, 1, 0), W.tm0np_omega(0.5, 1.0, 1, 1)
+    rows = []
+    for level, tau in SPAI_SWEEP:
+        mesh = pic.pic_mesh_create(*cav, precision=pic.PIC_FP64)
+        edges = pic.pic_mesh_edges(mesh)
+        P0 = W.tm0np_edge_dofs(cav[0], edges, 0.5, 1.0, 1, 0)
+        P1 = W.tm0np_edge_dofs(cav[0], edges, 0.5, 1.0, 1, 1)
+        dt_max = pic.pic_spai_build(mesh, level, tau)
+        info = pic.pic_spai_info(mesh)
+        n_free = pic.pic_mesh_info(mesh)["n_free_edges"]
+        dt = 0.5 * dt_max
+        sim = pic.pic_sim_create(mesh, dt, 0.0, 16)
+        pic.pic_fields_set(sim, P0 + P1, np.zeros(len(cav[1])))
+        a0, a1 = np.zeros(1000), np.zeros(1000)
+        for k in range(1000):
+            E, _ = pic.pic_fields_get(sim)
+            a0[k], a1[k] = E @ P0, E @ P1
+            pic.pic_step(sim, 1)
+        t = np.arange(1000) * dt
+        f0 = _dominant_frequency(t, a0, w010, w011)
+        f1 = _dominant_frequency(t, a1, w011, w010)
+        pic.pic_sim_destroy(sim)
+        pic.pic_mesh_destroy(mesh)
+
+        bm = pic.pic_mesh_create(wl["nodes"], wl["tris"], wl["be"], wl["bt"], eps0=EPS0,
+                                 mu0=MU0, c=C0, precision=pic.PIC_FP32)
+        bdt = pic.pic_spai_build(bm, level, tau)
+        binfo = pic.pic_spai_info(bm)
+        bfree = pic.pic_mesh_info(bm)["n_free_edges"]
+        bs = pic.pic_sim_create(bm, 0.5 * bdt, wl["bz"], 16)
+        pic.pic_sim_set_graph(bs, True)
+        pic.pic_fields_set(bs, bwo_edge_field(pic.pic_mesh_info(bm)["n_edges"], wl["e_scale"], 7),
+                           np.zeros(len(wl["tris"])))
+        pic.pic_step(bs, 100)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pic.pic_step(bs, 2000)
+        e1.record()
+        torch.cuda.synchronize()
+        step_us = e0.elapsed_time(e1) / 2000 * 1e3
+        pic.pic_sim_destroy(bs)
+        pic.pic_mesh_destroy(bm)
+        rows.append({"level": level, "drop_tol": tau,
+                     "cavity": {"nnz_per_row": info["nnz"] / n_free,
+                                "residual_rms": info["residual_rms"], "dt_stable": dt_max,
+                                "tm010_rel_err": (f0 - w010) / w010,
+                                "tm011_rel_err": (f1 - w011) / w011},
+                     "bwo": {"nnz_per_row": binfo["nnz"] / bfree,
+                             "residual_rms": binfo["residual_rms"], "dt_stable_s": bdt,
+                             "field_step_us": step_us,
+                             "sim_time_per_us_of_gpu": 0.5 * bdt / (step_us * 1e-6)}})
+    print(json.dumps({"metric": "SPAI sweep: field-update accuracy and cost", "rows": rows,
+                      "config": {"cavity": "0.5 x 1 normalised, %d triangles" % len(cav[1]),
+                                 "bwo": "%d triangles, FP32, no particles" % len(wl["tris"])}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +551,8 @@ def main():
     ap.add_argument("--surrogate-steps", type=int, default=4000)
     ap.add_argument("--mlp-queries", type=int, default=0,
                     help="time surrogate-network inference on this many queries instead")
+    ap.add_argument("--spai-sweep", action="store_true",
+                    help="SPAI pattern / drop-tolerance sweep (accuracy and cost) instead")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the launch-shape autotuner (fixed re-sort interval and shapes)")
     ap.add_argument("--no-graph", action="store_true",
@@ -479,6 +566,8 @@ def main():
         return run_surrogate(args)
     if args.mlp_queries:
         return run_mlp_queries(args)
+    if args.spai_sweep:
+        return run_spai_sweep(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

@@ -147,6 +147,13 @@ pic_status pic_spai_build(pic_mesh *m, int32_t pattern_level, double drop_tol,
 pic_status pic_spai_get(const pic_mesh *m, int32_t *free_edges, int64_t *indptr,
                         int32_t *indices, double *values);
 
+/* Quality of the SPAI (Sec. 3.1; not an operation of the paper): nnz of M, and the
+ * residual R = star_eps_ff M - I over the free edges, as ||R||_F / sqrt(n_free) (the RMS
+ * of the per-column residual norms) and max |R_ij|.  Host-only; each output may be NULL.
+ * Errors: STATE (no SPAI built). */
+pic_status pic_spai_info(const pic_mesh *m, int64_t *nnz, double *residual_rms,
+                         double *residual_max);
+
 /* Simulation on the current CUDA device: uploads the mesh operators and allocates
  * fields and room for `max_particles` particles.  dt must not exceed the stable step
  * from pic_spai_build (PIC_ERR_UNSTABLE otherwise); bz_guide is a uniform static axial

@@ -241,3 +241,50 @@ extern "C" pic_status pic_spai_get(const pic_mesh *pm, int32_t *free_edges, int6
     if (values) std::copy(m.M_val.begin(), m.M_val.end(), values);
     return PIC_OK;
 }
+
+extern "C" pic_status pic_spai_info(const pic_mesh *pm, int64_t *nnz, double *residual_rms,
+                                    double *residual_max) {
+    if (!pm || !pm->h.have_spai) {
+        set_error("pic_spai_info: no SPAI built");
+        return PIC_ERR_STATE;
+    }
+    const HostMesh &m = pm->h;
+    const int64_t nf = (int64_t)m.free_edges.size();
+    // R = A_ff M - I row by row (A_ff: star_eps restricted to the free edges), with a dense
+    // accumulator over the free edges
+    std::vector<double> acc(nf, 0.0);
+    std::vector<char> mark(nf, 0);
+    std::vector<int32_t> touched;
+    touched.reserve(256);
+    double ss = 0.0, mx = 0.0;
+    for (int64_t i = 0; i < nf; i++) {
+        const int32_t ei = m.free_edges[i];
+        touched.push_back((int32_t)i);   // the identity's entry
+        mark[i] = 1;
+        for (int64_t q = m.eps_ptr[ei]; q < m.eps_ptr[ei + 1]; q++) {
+            const int32_t k = m.free_of_edge[m.eps_idx[q]];
+            if (k < 0) continue;
+            const double a = m.eps_val[q];
+            for (int64_t r = m.M_ptr[k]; r < m.M_ptr[k + 1]; r++) {
+                const int32_t j = m.M_idx[r];
+                if (!mark[j]) {
+                    mark[j] = 1;
+                    touched.push_back(j);
+                }
+                acc[j] += a * m.M_val[r];
+            }
+        }
+        for (int32_t j : touched) {
+            const double v = acc[j] - (j == i ? 1.0 : 0.0);
+            ss += v * v;
+            mx = std::max(mx, std::fabs(v));
+            acc[j] = 0.0;
+            mark[j] = 0;
+        }
+        touched.clear();
+    }
+    if (nnz) *nnz = (int64_t)m.M_val.size();
+    if (residual_rms) *residual_rms = nf > 0 ? std::sqrt(ss / (double)nf) : 0.0;
+    if (residual_max) *residual_max = mx;
+    return PIC_OK;
+}

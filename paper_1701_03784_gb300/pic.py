@@ -61,6 +61,7 @@ _SIGS = {
     "pic_mesh_edges": [_P, _P],
     "pic_spai_build": [_P, _I32, _D, _P],
     "pic_spai_get": [_P, _P, _P, _P, _P],
+    "pic_spai_info": [_P, _P, _P, _P],
     "pic_sim_create": [_P, _D, _D, _I64, _P],
     "pic_sim_set_sort_interval": [_P, _I32],
     "pic_sim_set_pusher": [_P, _I32],
@@ -243,6 +244,15 @@ def pic_spai_build(mesh, pattern_level=2, drop_tol=1e-4):
     _check(_lib.pic_spai_build(mesh.ptr, pattern_level, drop_tol, ctypes.byref(dt)),
            "pic_spai_build")
     return dt.value
+
+
+def pic_spai_info(mesh):
+    """{nnz, residual_rms, residual_max} of M against star_eps on the free edges."""
+    nnz = _I64()
+    rms, mx = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.pic_spai_info(mesh.ptr, ctypes.byref(nnz), ctypes.byref(rms), ctypes.byref(mx)),
+           "pic_spai_info")
+    return {"nnz": nnz.value, "residual_rms": rms.value, "residual_max": mx.value}
 
 
 def pic_spai_get(mesh):
