@@ -15,6 +15,8 @@ Layout:
   particles.py  ctypes wrapper around particles.c and the point-location used at
                 injection.
   sim.py        one PIC cycle in the order of Sec. 3 (field, gather, push, scatter).
+  sources.py    static gun field (Laplace problem), cathode emission with counter-based
+                draws, planar space-charge-limited current (Secs. 5.2, 5.3).
 
 Every function's pin (what fixes it other than itself) is listed in tests/test_oracle_*.py.
 """

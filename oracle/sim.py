@@ -2,9 +2,10 @@
 
 State at the start of step n: E^n (edges), B^{n-1/2} (faces), particle positions r^n
 (triangle + barycentric lambda), momenta u^{n-1/2}, node charges Q^n.
+  0. emission (optional): new particles at r^n with u^{n-1/2}, their charge added to Q^n
   1. B^{n+1/2} = B^{n-1/2} - dt D_curl E^n                        (Eq. full_d_dfl)
-  2. gather E^n and (B^{n+1/2} + B^{n-1/2})/2 at r^n, push (Boris or Vay), walk, scatter
-     J^{n+1/2} (Eq. current) and Q^{n+1} (Eq. charge)              (Secs. 3.2-3.4)
+  2. gather E^n (+ a static field) and (B^{n+1/2} + B^{n-1/2})/2 at r^n, push (Boris or
+     Vay), walk, scatter J^{n+1/2} (Eq. current) and Q^{n+1} (Eq. charge) (Secs. 3.2-3.4)
   3. E^{n+1} = E^n + dt M (D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}) (Eq. full_d_dal)
 The auxiliary dual flux D^{n+1} = D^n + dt (D_curl^T star_mu^-1 B^{n+1/2} - J^{n+1/2}) is
 carried for the discrete Gauss law check: D_div D^n - Q^n is constant in n (Sec. 3.5.2).
@@ -15,6 +16,7 @@ import numpy as np
 
 from .operators import Mesh, hodge_eps, hodge_mu_inv, spai, dt_stable, field_energy
 from . import particles as P
+from . import sources as S
 
 
 class OracleSim:
@@ -47,6 +49,9 @@ class OracleSim:
         self.pusher = P.BORIS   # velocity update of Eq. DLE: P.BORIS or P.VAY
         self.counters = np.zeros(3, np.int64)
         self.n = 0
+        self.E_static = None    # static (gun) field added at the gather, or None
+        self.emitter = None     # dict of emitted() arguments and the species, or None
+        self.Q_born = np.zeros(self.mesh.N0)   # charge of emitted particles, per node
 
     def create(self, dt, bz=0.0):
         if dt > self.dt_max:
@@ -77,6 +82,28 @@ class OracleSim:
         self.lam = np.ascontiguousarray(np.concatenate([self.lam, lam]))
         self.u = np.ascontiguousarray(np.concatenate([self.u, u]))
 
+    def set_static_field(self, E_static):
+        """A static field (edge values, e.g. from sources.static_potential) added to E^n
+        at the gather only: it drives the particles but takes no part in the leapfrog."""
+        self.E_static = None if E_static is None else np.array(E_static, float)
+
+    def set_emitter(self, z0, rho0, rho1, per_step, u_normal, u_thermal, seed, q, mass,
+                    weight):
+        """Emit per_step particles at the start of every step (sources.emitted, ids
+        continuing the particle count)."""
+        self.emitter = dict(z0=z0, rho0=rho0, rho1=rho1, per_step=int(per_step),
+                            u_normal=u_normal, u_thermal=u_thermal, seed=int(seed), q=q,
+                            mass=mass, weight=weight)
+
+    def emit(self):
+        em = self.emitter
+        pids = np.arange(len(self.tri), len(self.tri) + em["per_step"])
+        z, r, ur, up, uz = S.emitted(em["z0"], em["rho0"], em["rho1"], em["u_normal"],
+                                     em["u_thermal"], em["seed"], pids)
+        q0 = self.Q.copy()
+        self.inject(z, r, ur, up, uz, em["q"], em["mass"], em["weight"])
+        self.Q_born += self.Q - q0
+
     def field_b_half(self):
         """Eq. full_d_dfl."""
         return self.B - self.dt * (self.mesh.Dcurl @ self.E)
@@ -87,7 +114,8 @@ class OracleSim:
         self.J = np.zeros(m.N1)
         Qn = np.zeros(m.N0)
         self.Qabs = np.zeros(m.N0)
-        cnt = P.push(self.pm, self.E, Bavg, self.bz, self.dt, self.qm, self.c, self.q_src,
+        Eg = self.E if self.E_static is None else self.E + self.E_static
+        cnt = P.push(self.pm, Eg, Bavg, self.bz, self.dt, self.qm, self.c, self.q_src,
                      self.tri, self.lam, self.u, self.J, Qn, self.Qabs, pusher=self.pusher)
         self.counters += cnt
         return Qn
@@ -102,6 +130,8 @@ class OracleSim:
 
     def step(self, n=1):
         for _ in range(n):
+            if self.emitter is not None:
+                self.emit()
             B_half = self.field_b_half()
             Qn = self.push_particles(B_half)
             self.field_e(B_half)
@@ -115,10 +145,11 @@ class OracleSim:
         return (self.Q - self.Q_prev + self.Qabs) / self.dt + self.mesh.Ddiv @ self.J
 
     def dgl_residual(self):
-        """D_div D^n - Q^n at nodes not on a conducting wall (Eq. DGL_RSD_REL)."""
+        """D_div D^n - Q^n at nodes not on a conducting wall (Eq. DGL_RSD_REL), with the
+        charge of emitted particles (born without a current) taken out of Q^n."""
         m = self.mesh
         f = m.free
-        res = m.Ddiv[:, f] @ self.D[f] - self.Q
+        res = m.Ddiv[:, f] @ self.D[f] - (self.Q - self.Q_born)
         res[m.node_on_pec] = 0.0
         return res
 
