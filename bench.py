@@ -529,6 +529,37 @@ def run_spai_sweep(args):
     return 0
 
 
+def run_diode(args):
+    """Planar diode at 100 kV over 1 cm with a 6 cm emitter (Sec. 5.2's check on a planar
+    gap): the largest injection that forms no virtual cathode (no particle returns to the
+    cathode), bracketed by a scan of injection currents, against the classical
+    Child-Langmuir closed form; and the run's throughput."""
+    import torch
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import diode
+    rows = []
+    t0 = time.perf_counter()
+    for f in (0.90, 0.95, 1.00, 1.05, 1.10, 1.20):
+        r = diode.run(over=f)
+        rows.append({"inject_over_classical": f, "return_fraction": r["return_fraction"],
+                     "I_anode_over_I_emitted": r["I_anode"] / r["I_emitted"],
+                     "J_center_over_classical": r["J_center"] / r["J_classical"],
+                     "n_particles_end": r["n_particles"], "steps": r["steps"],
+                     "emit_dropped": r["emit_dropped"], "dce_nonzero": r["dce_nonzero"]})
+    wall = time.perf_counter() - t0
+    clean = [x["inject_over_classical"] for x in rows if x["return_fraction"] == 0.0]
+    vc = [x["inject_over_classical"] for x in rows if x["return_fraction"] > 0.0]
+    print(json.dumps({"metric": "planar diode: space-charge limit bracket / classical "
+                                "Child-Langmuir", "unit": "ratio",
+                      "value": [max(clean) if clean else None, min(vc) if vc else None],
+                      "rows": rows, "wall_s": wall,
+                      "config": {"workload": "planar diode 100 kV, 1 cm gap, 7 cm wall, 6 cm "
+                                             "emitter, 35k triangles, 500 births per step, "
+                                             "FP32, 8000 + 6000 steps per injection"}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -553,6 +584,8 @@ def main():
                     help="time surrogate-network inference on this many queries instead")
     ap.add_argument("--spai-sweep", action="store_true",
                     help="SPAI pattern / drop-tolerance sweep (accuracy and cost) instead")
+    ap.add_argument("--diode", action="store_true",
+                    help="planar space-charge-limited diode (static field + emission) instead")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the launch-shape autotuner (fixed re-sort interval and shapes)")
     ap.add_argument("--no-graph", action="store_true",
@@ -568,6 +601,8 @@ def main():
         return run_mlp_queries(args)
     if args.spai_sweep:
         return run_spai_sweep(args)
+    if args.diode:
+        return run_diode(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

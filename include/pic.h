@@ -99,6 +99,8 @@ typedef struct {
     double field_energy;     /* 1/2 E.star_eps.E + 1/2 B.star_mu^-1.B (per radian)        */
     double kinetic_energy;   /* sum (gamma-1) m c^2 w over live particles (3D)             */
     double q_absorbed;       /* charge removed at walls since creation (3D, q*w units)   */
+    int64_t n_emitted;       /* particles born by the emitter since creation              */
+    int64_t emit_dropped;    /* particles the emitter did not make for lack of capacity   */
 } pic_diag;
 
 /* Allocator hook for device memory (e.g. a framework's caching allocator).  alloc must
@@ -176,6 +178,46 @@ pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
  * Errors: ARG (null handle or unknown pusher). */
 enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
 pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher);
+
+/* Sources either side of the particle loop (Secs. 5.2, 5.3).
+ *
+ * The static (gun) field of the electrodes: the node potential phi with phi held at
+ * held_nodes (n_held of them, potentials held_phi) and D_div star_eps D_div^T phi = 0 at
+ * every other node, i.e. the discrete Gauss law without charge for E = -grad phi, whose
+ * Whitney-1 edge values are phi(tail) - phi(head) (zero normal flux where no potential is
+ * held).  Solved on the host by conjugate gradients; phi_out (N0) and E_out (N1) may each
+ * be NULL.  Errors: ARG, MESH (a part of the mesh reaches no held node). */
+pic_status pic_static_potential(const pic_mesh *m, int64_t n_held, const int32_t *held_nodes,
+                                const double *held_phi, double *phi_out, double *E_out);
+
+/* A static field (N1 edge values, e.g. E_out above) added to E^n at the gather only: it
+ * drives the particles but takes no part in the leapfrog (the electrodes' voltage is held
+ * by it, the self-field sees grounded conductors).  NULL removes it.  Copied; synchronous.
+ * Errors: ARG (not finite), OOM, CUDA. */
+pic_status pic_sim_set_static_field(pic_sim *s, const double *E_static, void *cuda_stream);
+
+/* Emission: at the start of every step, before the particle kernel, per_step particles
+ * are born on the line z = z (inside the mesh, crossing no node), rho uniform in area over
+ * [rho0, rho1]; momenta u = gamma v with independent normal components of standard
+ * deviation u_thermal about (0, 0, u_normal).  Their charge is added to Q^n at the birth
+ * point (Eq. charge), so Eq. DCE holds for the step, and is taken out of the Gauss-law
+ * drift.  Draws are counter-based: for particle id p and draw j (0: rho, 1-2 and 3-4:
+ * Box-Muller pairs), splitmix64(seed + 8 p + j) >> 11 as (k + 1/2) 2^-53.  Particle ids
+ * continue the count of all particles made.  A step whose births do not fit the capacity
+ * makes none (counted in pic_diag.emit_dropped).  One species per simulation (q/m and
+ * q*w as for pic_particles_inject).  While an emitter is set, launches are sized for the
+ * capacity.  NULL stops emission.  Not in the paper's equations: the paper injects at
+ * the cathode without giving the distribution.  Errors: ARG, OOM, CUDA. */
+typedef struct {
+    double z;          /* emission line z = const                                   */
+    double rho0, rho1; /* radial extent                                             */
+    int64_t per_step;  /* particles born per step                                   */
+    double u_normal;   /* mean u_z of the new particles                             */
+    double u_thermal;  /* standard deviation of each momentum component             */
+    uint64_t seed;     /* generator key                                             */
+    double q, m, w;    /* species: charge, mass, macro-particle weight              */
+} pic_emitter;
+pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *cuda_stream);
 
 /* Replay steps from a CUDA graph (off by default).  pic_step then records one period of
  * 2 x the re-sort interval steps (2 with re-sorting off) on an internal stream the first
@@ -283,8 +325,8 @@ pic_status pic_particles_raw_set(pic_sim *s, const void *host_src, int64_t n_slo
  * re-sort removed particles are unspecified on return.  The download of one step runs on
  * an internal stream and overlaps, chunk by chunk, the upload of the next; the call is
  * asynchronous on cuda_stream, which waits for the last download.  Errors: PIC_ERR_ARG
- * (null state, bad counts), PIC_ERR_CUDA.  The host buffer must stay untouched until the
- * stream reaches that point. */
+ * (null state, bad counts), PIC_ERR_STATE (an emitter is set: the slot count would grow),
+ * PIC_ERR_CUDA.  The host buffer must stay untouched until the stream reaches that point. */
 pic_status pic_step_host(pic_sim *s, void *host_state, int64_t n_slots, int64_t n_steps,
                          void *cuda_stream);
 

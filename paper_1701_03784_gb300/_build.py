@@ -8,8 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic_gb300.so")
-SOURCES = ["mesh.cpp", "spai.cpp", "sim.cu", "k_push.cu", "k_push_f32.cu", "k_field.cu", "k_sort.cu",
-           "k_diag.cu", "mlp.cu", "k_mlp_tc.cu"]
+SOURCES = ["mesh.cpp", "spai.cpp", "sources.cpp", "sim.cu", "k_push.cu", "k_push_f32.cu", "k_field.cu",
+           "k_sort.cu", "k_diag.cu", "k_emit.cu", "mlp.cu", "k_mlp_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

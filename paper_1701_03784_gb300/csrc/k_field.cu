@@ -8,7 +8,9 @@ namespace pic {
 
 // K3, one thread per face: B^{n+1/2} = B^{n-1/2} - dt (D_curl E^n)_f, and the record's
 // field coefficients: E(lambda) = sum_k E_k (lambda_a grad lambda_b - lambda_b grad
-// lambda_a) = sum_m lambda_m c_m, and B_phi = (B^{n+1/2} + B^{n-1/2}) / (2A) (W2 = 1/A).
+// lambda_a) = sum_m lambda_m c_m (E_k plus the static field's edge value when one is set:
+// it drives the particles but takes no part in the leapfrog), and
+// B_phi = (B^{n+1/2} + B^{n-1/2}) / (2A) (W2 = 1/A).
 // The same launch clears the step's accumulators (J per edge, Q_abs per node, and in the
 // FP64 build Q^{n+1}, which the particle kernel accumulates).
 template <class P>
@@ -31,12 +33,16 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
         float c[3][2] = {{0, 0}, {0, 0}, {0, 0}};
         float curl = 0;
         const int ek[3] = {EG.x, EG.y, EG.z};
-        float E3[3];
+        float E3[3], S3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 3; k++) E3[k] = a.E[ek[k]];
+        if (a.Es) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) S3[k] = a.Es[ek[k]];
+        }
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const float Ek = E3[k];
+            const float Ek = a.Es ? E3[k] + S3[k] : E3[k];   // the gather sees the static field
             const int i = (k + 1) % 3, j = (k + 2) % 3;
             const bool fwd = (EG.w >> k) & 1;
             const int ta = fwd ? i : j, hb = fwd ? j : i;
@@ -44,7 +50,7 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
             c[ta][1] += Ek * g[hb][1];
             c[hb][0] -= Ek * g[ta][0];
             c[hb][1] -= Ek * g[ta][1];
-            curl += fwd ? Ek : -Ek;
+            curl += fwd ? E3[k] : -E3[k];
         }
         const float Bold = a.B[f];
         const float Bnew = Bold - a.dt * curl;
@@ -60,7 +66,8 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
     R curl = 0;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        R Ek = a.E[rc.edge[k]];
+        const R Ed = a.E[rc.edge[k]];
+        const R Ek = a.Es ? Ed + a.Es[rc.edge[k]] : Ed;   // the gather sees the static field
         int i = (k + 1) % 3, j = (k + 2) % 3;
         bool fwd = (flags >> k) & 1;   // edge runs (k+1) -> (k+2): D_curl entry +1
         int ta = fwd ? i : j, hb = fwd ? j : i;
@@ -68,7 +75,7 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
         c[ta][1] += Ek * g[hb][1];
         c[hb][0] -= Ek * g[ta][0];
         c[hb][1] -= Ek * g[ta][1];
-        curl += fwd ? Ek : -Ek;
+        curl += fwd ? Ed : -Ed;
     }
     R Bold = a.B[f];
     R Bnew = Bold - a.dt * curl;

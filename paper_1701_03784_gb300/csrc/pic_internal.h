@@ -134,6 +134,13 @@ void parallel_for(int64_t n, F &&f) {
 void build_locator(HostMesh &m);
 // containing triangle (largest smallest barycentric coordinate) or -1; lam[3] out
 int32_t locate_point(const HostMesh &m, double z, double rho, double lam[3]);
+// intervals of the line z = z0, rho in [rho0, rho1], per triangle crossed (sorted, with
+// the barycentric coordinates at both ends); false if the line leaves the mesh, passes
+// through a node's z or the intervals do not tile [rho0, rho1]
+bool build_emit_line(const HostMesh &m, double z0, double rho0, double rho1,
+                     std::vector<double> &rho_a, std::vector<double> &rho_b,
+                     std::vector<double> &lam_a, std::vector<double> &lam_b,
+                     std::vector<int32_t> &tri);
 
 // ---------------------------------------------------------------------------------
 // device layouts
@@ -188,6 +195,9 @@ enum {
     CNT_CROSSINGS = 2,
     CNT_REMAINDER = 3,  // nodes where D_div J was not a multiple of 2^22 (must stay 0)
     CNT_TIMEOUT = 4,    // bounded device waits that gave up (must stay 0)
+    CNT_EMITTED = 5,    // particles born by the emitter
+    CNT_NEXT_PID = 6,   // next particle id once an emitter was set
+    CNT_EMIT_DROPPED = 7,   // particles the emitter did not make for lack of room
     CNT_N = 8
 };
 // slots past the capacity that the particle arrays keep for 16-byte bulk-copy rounding
@@ -211,10 +221,37 @@ struct PushArgs {
     int32_t pusher;             // PIC_PUSHER_BORIS or PIC_PUSHER_VAY (Eq. DLE)
 };
 
+// Emission line z = const, cut into the triangles it crosses: interval k spans
+// rho in [rho_a[k], rho_b[k]] inside triangle tri[k], with barycentric coordinates lam_a
+// and lam_b (3 each) at its ends (linear in between).
+struct EmitLine {
+    const double *rho_a, *rho_b, *lam_a, *lam_b;
+    const int32_t *tri;
+    int32_t n;
+};
+
+template <class P>
+struct EmitArgs {
+    EmitLine line;
+    Particles<P> p;
+    const TriRec<typename P::R> *rec;
+    int64_t *n_slots;
+    unsigned long long *counters;
+    typename P::Acc *Qn;        // Q^n: the births' charge is added here
+    typename P::Acc *Qwall;     // and taken out of the Gauss-law bookkeeping here
+    int64_t cap, per_step;
+    double rho0, rho1, u_normal, u_thermal;
+    unsigned long long seed;
+};
+
+template <class P>
+void launch_emit(const EmitArgs<P> &a, cudaStream_t s);
+
 template <class P>
 struct FieldArgs {
     TriRec<typename P::R> *rec;
     typename P::R *E;           // N1
+    const typename P::R *Es;    // N1 static field added at the gather only, or null
     typename P::R *B;           // N2, B^{n-1/2} in, B^{n+1/2} out
     const typename P::R *mu_inv;// N2
     const int32_t *edge_face;   // nf x 2, per free edge: (face+1) * sign, 0 if none

@@ -71,6 +71,8 @@ struct SimBase {
     virtual pic_status autotune(int32_t trial, pic_tuning *out, cudaStream_t s) = 0;
     virtual pic_status timing(int enable, double *ms, int64_t *launches, cudaStream_t s) = 0;
     virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
+    virtual pic_status set_static_field(const double *E, cudaStream_t s) = 0;
+    virtual pic_status set_emitter(const pic_emitter *e, cudaStream_t s) = 0;
     int32_t sort_interval = 16;
     int32_t pusher = PIC_PUSHER_BORIS;
     int device = 0;
@@ -107,6 +109,15 @@ struct SimImpl final : SimBase {
     SortScratch sc;
     DiagDev dd{};
     double *dgl_ref = nullptr, *diag_out = nullptr;
+    // sources (Secs. 5.2, 5.3): a static field added at the gather, and an emitter
+    R *Es = nullptr;
+    bool static_on = false, emitting = false, emitter_ever = false;
+    pic_emitter em{};
+    EmitLine eline{};
+    double *el_buf = nullptr;
+    int32_t *el_tri = nullptr;
+    int64_t el_room = 0;
+    int src_version = 0;
 
     bool timing_on = false;
     // host round trips (step_host): uploads and downloads run on streams of their own,
@@ -120,7 +131,8 @@ struct SimImpl final : SimBase {
     int32_t tune_ctas = 0, tune_block = 256;
     cudaStream_t g_stream = nullptr;
     cudaGraphExec_t g_exec = nullptr;
-    int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1, g_ctas = -1, g_block = -1, g_pusher = -1;
+    int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1, g_ctas = -1, g_block = -1, g_pusher = -1,
+        g_src = -1;
     int64_t g_bound = -1;
     cudaStream_t rt_stream = nullptr, up_stream = nullptr;
     cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr, rt_up = nullptr;
@@ -349,7 +361,90 @@ struct SimImpl final : SimBase {
         a.counters = counters;
         a.N0 = m->N0;
         a.block = tune_block;
+        a.Es = static_on ? Es : nullptr;
         return a;
+    }
+
+    pic_status set_static_field(const double *Eh, cudaStream_t s) override {
+        src_version++;
+        if (!Eh) {
+            static_on = false;
+            return PIC_OK;
+        }
+        std::vector<R> e(m->N1);
+        for (int64_t i = 0; i < m->N1; i++) {
+            if (!std::isfinite(Eh[i])) {
+                set_error("pic_sim_set_static_field: edge value %lld is not finite", (long long)i);
+                return PIC_ERR_ARG;
+            }
+            e[i] = (R)Eh[i];
+        }
+        pic_status st;
+        if (!Es && (st = dalloc(Es, m->N1)) != PIC_OK) return st;
+        PIC_CUDA_TRY(cudaMemcpyAsync(Es, e.data(), sizeof(R) * m->N1, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        static_on = true;
+        return PIC_OK;
+    }
+
+    pic_status set_emitter(const pic_emitter *e, cudaStream_t s) override {
+        src_version++;
+        if (!e) {
+            emitting = false;
+            return PIC_OK;
+        }
+        if (e->per_step < 0 || !(e->rho0 >= 0.0) || !(e->rho1 > e->rho0) || !std::isfinite(e->z) ||
+            !std::isfinite(e->u_normal) || !(e->u_thermal >= 0.0) || !(e->m > 0) || !(e->w > 0) ||
+            !std::isfinite(e->q)) {
+            set_error("pic_sim_set_emitter: bad argument");
+            return PIC_ERR_ARG;
+        }
+        const double qsrc = e->w * e->q / (2.0 * M_PI);
+        if (have_species && (e->q / e->m != qm || qsrc != q_src)) {
+            set_error("pic_sim_set_emitter: one species per simulation (q/m and q*w must match)");
+            return PIC_ERR_ARG;
+        }
+        std::vector<double> ra, rb, la, lb;
+        std::vector<int32_t> tr;
+        if (!build_emit_line(*m, e->z, e->rho0, e->rho1, ra, rb, la, lb, tr)) {
+            set_error("pic_sim_set_emitter: the line z = %g, rho in [%g, %g] does not lie inside "
+                      "the mesh, or meets a node", e->z, e->rho0, e->rho1);
+            return PIC_ERR_ARG;
+        }
+        const int64_t n = (int64_t)tr.size();
+        pic_status st;
+        if (n > el_room) {
+            if ((st = dalloc(el_buf, 8 * n)) != PIC_OK || (st = dalloc(el_tri, n)) != PIC_OK) return st;
+            el_room = n;
+        }
+        std::vector<double> buf(8 * n);
+        std::copy(ra.begin(), ra.end(), buf.begin());
+        std::copy(rb.begin(), rb.end(), buf.begin() + n);
+        std::copy(la.begin(), la.end(), buf.begin() + 2 * n);
+        std::copy(lb.begin(), lb.end(), buf.begin() + 5 * n);
+        PIC_CUDA_TRY(cudaMemcpyAsync(el_buf, buf.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(el_tri, tr.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+        if (!emitter_ever) {
+            // particle ids continue on the device from here on
+            unsigned long long np = (unsigned long long)next_pid;
+            PIC_CUDA_TRY(cudaMemcpyAsync(counters + CNT_NEXT_PID, &np, sizeof np, cudaMemcpyHostToDevice, s));
+        }
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        eline = EmitLine{el_buf, el_buf + n, el_buf + 2 * n, el_buf + 5 * n, el_tri, (int32_t)n};
+        em = *e;
+        if (!have_species) {
+            have_species = true;
+            q = e->q;
+            mass = e->m;
+            weight = e->w;
+            qm = e->q / e->m;
+            q_src = qsrc;
+        }
+        emitting = true;
+        emitter_ever = true;
+        // launches cover the whole capacity from now on (the kernels read the live count)
+        n_bound = cap;
+        return PIC_OK;
     }
 
     pic_status fields_set(const double *Eh, const double *Bh, cudaStream_t s) override {
@@ -416,6 +511,13 @@ struct SimImpl final : SimBase {
             set_error("pic_particles_inject: capacity %lld exceeded", (long long)cap);
             return PIC_ERR_OOM;
         }
+        if (emitter_ever) {
+            // the emitter numbers particles on the device: continue from its count
+            unsigned long long np = 0;
+            PIC_CUDA_TRY(cudaMemcpyAsync(&np, counters + CNT_NEXT_PID, sizeof np, cudaMemcpyDeviceToHost, s));
+            PIC_CUDA_TRY(cudaStreamSynchronize(s));
+            next_pid = (int64_t)np;
+        }
         std::vector<int32_t> tri(n), pid(n);
         std::vector<Lam> l0(n), l1(n);
         std::vector<R> vr(n), vp(n), vz(n);
@@ -476,8 +578,12 @@ struct SimImpl final : SimBase {
         int64_t n_new = n_now + n;
         PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n_new, sizeof(int64_t), cudaMemcpyHostToDevice, s));
         launch_deposit_q<P>(rec, p, n_now, n, Qn(), s);
-        n_bound = n_new;
+        n_bound = emitting ? cap : n_new;
         next_pid += n;
+        if (emitter_ever) {
+            unsigned long long np = (unsigned long long)next_pid;
+            PIC_CUDA_TRY(cudaMemcpyAsync(counters + CNT_NEXT_PID, &np, sizeof np, cudaMemcpyHostToDevice, s));
+        }
         n_injected += n;
         resort(s);
         PIC_CUDA_TRY(cudaGetLastError());
@@ -515,7 +621,7 @@ struct SimImpl final : SimBase {
             }
             // a graph records the launch shapes and the pusher with the buffers
             if (g_exec && (g_bound != n_bound || g_interval != sort_interval || g_ctas != tune_ctas ||
-                           g_block != tune_block || g_pusher != pusher)) {
+                           g_block != tune_block || g_pusher != pusher || g_src != src_version)) {
                 cudaGraphExecDestroy(g_exec);
                 g_exec = nullptr;
             }
@@ -606,6 +712,7 @@ struct SimImpl final : SimBase {
         g_ctas = tune_ctas;
         g_block = tune_block;
         g_pusher = pusher;
+        g_src = src_version;
         PIC_CUDA_TRY(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
         pic_status st = step_direct(L, g_stream);
         cudaGraph_t graph = nullptr;
@@ -639,6 +746,24 @@ struct SimImpl final : SimBase {
                 launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, Qwall, D, dgl_ref, 1, E, B, mu_inv,
                                parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
                 dgl_dirty = false;
+            }
+            if (emitting) {
+                EmitArgs<P> ea;
+                ea.line = eline;
+                ea.p = parts[cur];
+                ea.rec = rec;
+                ea.n_slots = d_n;
+                ea.counters = counters;
+                ea.Qn = Qn();
+                ea.Qwall = Qwall;
+                ea.cap = cap;
+                ea.per_step = em.per_step;
+                ea.rho0 = em.rho0;
+                ea.rho1 = em.rho1;
+                ea.u_normal = em.u_normal;
+                ea.u_thermal = em.u_thermal;
+                ea.seed = (unsigned long long)em.seed;
+                launch_emit<P>(ea, s);
             }
             Acc *Qnext = Qbuf[1 - qcur];
             // the face kernel clears J, Q_abs and (FP64) Q^{n+1}; in the FP32 build Q^{n+1} is
@@ -767,7 +892,9 @@ struct SimImpl final : SimBase {
             o->n_absorbed = (int64_t)cnt[CNT_ABSORBED];
             o->walk_overflows = (int64_t)cnt[CNT_OVERFLOW];
             o->n_crossings = (int64_t)cnt[CNT_CROSSINGS];
-            o->n_particles = n_injected - (int64_t)cnt[CNT_ABSORBED];
+            o->n_particles = n_injected + (int64_t)cnt[CNT_EMITTED] - (int64_t)cnt[CNT_ABSORBED];
+            o->n_emitted = (int64_t)cnt[CNT_EMITTED];
+            o->emit_dropped = (int64_t)cnt[CNT_EMIT_DROPPED];
             o->n_steps = n_steps;
             o->dce_max = out[0];
             o->dce_nonzero = (int64_t)out[1] + (int64_t)cnt[CNT_REMAINDER];
@@ -843,7 +970,7 @@ struct SimImpl final : SimBase {
 
     pic_status count(int64_t *n, cudaStream_t s) override {
         pic_status st = read_count(n, s);
-        if (st == PIC_OK) n_bound = std::min(n_bound, *n);
+        if (st == PIC_OK && !emitting) n_bound = std::min(n_bound, *n);
         return st;
     }
 
@@ -925,7 +1052,7 @@ struct SimImpl final : SimBase {
         h += sizeof(R) * n;
         PIC_CUDA_TRY(cudaMemcpyAsync(p.uz, h, sizeof(R) * n, cudaMemcpyHostToDevice, s));
         PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        n_bound = n;
+        n_bound = emitting ? cap : n;
         dgl_dirty = true;
         return PIC_OK;
     }
@@ -950,6 +1077,10 @@ struct SimImpl final : SimBase {
         if (!state || n < 0 || n > cap || steps < 0) {
             set_error("pic_step_host: bad argument");
             return PIC_ERR_ARG;
+        }
+        if (emitting) {
+            set_error("pic_step_host: the slot count of a host state cannot grow (emitter set)");
+            return PIC_ERR_STATE;
         }
         if (!rt_stream) {
             PIC_CUDA_TRY(cudaStreamCreateWithFlags(&rt_stream, cudaStreamNonBlocking));
@@ -979,7 +1110,7 @@ struct SimImpl final : SimBase {
             if (k == 0) {
                 // the caller's state: its slot count, and a new Gauss-law reference
                 PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-                n_bound = n;
+                n_bound = emitting ? cap : n;
                 dgl_dirty = true;
             }
             if ((st = step(1, s)) != PIC_OK) return st;
@@ -1103,6 +1234,16 @@ extern "C" pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher) {
     }
     s->impl->pusher = pusher;
     return PIC_OK;
+}
+
+extern "C" pic_status pic_sim_set_static_field(pic_sim *s, const double *E_static, void *st) {
+    SIM_CHECK(s, "pic_sim_set_static_field");
+    return s->impl->set_static_field(E_static, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *st) {
+    SIM_CHECK(s, "pic_sim_set_emitter");
+    return s->impl->set_emitter(e, (cudaStream_t)st);
 }
 
 extern "C" pic_status pic_fields_set(pic_sim *s, const double *E, const double *B, void *st) {

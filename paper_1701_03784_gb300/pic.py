@@ -40,7 +40,15 @@ class pic_diag(ctypes.Structure):
                 ("n_steps", ctypes.c_int64), ("dce_max", ctypes.c_double),
                 ("dce_nonzero", ctypes.c_int64), ("nr_dce_max", ctypes.c_double),
                 ("dgl_drift", ctypes.c_double), ("field_energy", ctypes.c_double),
-                ("kinetic_energy", ctypes.c_double), ("q_absorbed", ctypes.c_double)]
+                ("kinetic_energy", ctypes.c_double), ("q_absorbed", ctypes.c_double),
+                ("n_emitted", ctypes.c_int64), ("emit_dropped", ctypes.c_int64)]
+
+
+class pic_emitter(ctypes.Structure):
+    _fields_ = [("z", ctypes.c_double), ("rho0", ctypes.c_double), ("rho1", ctypes.c_double),
+                ("per_step", ctypes.c_int64), ("u_normal", ctypes.c_double),
+                ("u_thermal", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("q", ctypes.c_double), ("m", ctypes.c_double), ("w", ctypes.c_double)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -65,6 +73,9 @@ _SIGS = {
     "pic_sim_create": [_P, _D, _D, _I64, _P],
     "pic_sim_set_sort_interval": [_P, _I32],
     "pic_sim_set_pusher": [_P, _I32],
+    "pic_static_potential": [_P, _I64, _P, _P, _P, _P],
+    "pic_sim_set_static_field": [_P, _P, _P],
+    "pic_sim_set_emitter": [_P, ctypes.POINTER(pic_emitter), _P],
     "pic_sim_set_graph": [_P, _I32],
     "pic_sim_autotune": [_P, _I32, _P, _P],
     "pic_mlp_create": [_I32, _I32, _P, _I32, _P],
@@ -282,6 +293,38 @@ def pic_sim_create(mesh, dt, bz_guide=0.0, max_particles=0, torch_memory=True):
 
 def pic_sim_set_sort_interval(sim, interval):
     _check(_lib.pic_sim_set_sort_interval(sim.ptr, interval), "pic_sim_set_sort_interval")
+
+
+def pic_static_potential(mesh, held_nodes, held_phi):
+    """(phi on nodes, E_static on edges) of the electrodes: phi held at held_nodes,
+    discrete Laplace problem elsewhere (Sec. 5.3)."""
+    held_nodes = _arr(held_nodes, np.int32)
+    held_phi = _arr(np.broadcast_to(held_phi, held_nodes.shape), np.float64)
+    info = pic_mesh_info(mesh)
+    phi = np.zeros(info["n_nodes"])
+    E = np.zeros(info["n_edges"])
+    _check(_lib.pic_static_potential(mesh.ptr, len(held_nodes), _ptr(held_nodes),
+                                     _ptr(held_phi), _ptr(phi), _ptr(E)), "pic_static_potential")
+    return phi, E
+
+
+def pic_sim_set_static_field(sim, E_static, stream=None):
+    """Static field added at the gather (None removes it)."""
+    Es = None if E_static is None else _arr(E_static, np.float64)
+    _check(_lib.pic_sim_set_static_field(sim.ptr, _ptr(Es), _stream(stream)),
+           "pic_sim_set_static_field")
+
+
+def pic_sim_set_emitter(sim, z, rho0, rho1, per_step, u_normal, u_thermal, seed, q, m, w,
+                        stream=None):
+    """Emit per_step particles at the start of every step (see pic.h); per_step=None
+    stops emission."""
+    if per_step is None:
+        _check(_lib.pic_sim_set_emitter(sim.ptr, None, _stream(stream)), "pic_sim_set_emitter")
+        return
+    e = pic_emitter(z, rho0, rho1, per_step, u_normal, u_thermal, seed, q, m, w)
+    _check(_lib.pic_sim_set_emitter(sim.ptr, ctypes.byref(e), _stream(stream)),
+           "pic_sim_set_emitter")
 
 
 def pic_sim_set_pusher(sim, pusher):
