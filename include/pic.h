@@ -219,6 +219,19 @@ typedef struct {
 } pic_emitter;
 pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *cuda_stream);
 
+/* Absorbing layer (the paper ends its ports and left walls with a PML, Sec. 5.3, without
+ * giving its equations; this is a documented substitute): electric conductivity sigma_e
+ * per edge (N1, S/m) and magnetic conductivity sigma_m per face (N2, ohm/m), both >= 0,
+ * e.g. graded from 0 at the layer's inner face, sigma_m = sigma_e mu0 / eps0 for a
+ * matched layer.  With s = sigma_e dt / (2 eps0) the E update of Eq. full_d_dal becomes
+ * E <- (1 - s)/(1 + s) E + dt (M r) / (1 + s) on each free edge, and with
+ * s = sigma_m dt / (2 mu0) Eq. full_d_dfl becomes B <- (1 - s)/(1 + s) B - dt D_curl E
+ * / (1 + s) on each face (the conduction terms time-centred).  Conduction moves charge in
+ * the layer, so its nodes leave the Gauss-law drift (a new reference is taken).  Both
+ * NULL: lossless.  Copied; synchronous.  Errors: ARG (negative or not finite), OOM, CUDA. */
+pic_status pic_sim_set_loss(pic_sim *s, const double *sigma_e, const double *sigma_m,
+                            void *cuda_stream);
+
 /* Replay steps from a CUDA graph (off by default).  pic_step then records one period of
  * 2 x the re-sort interval steps (2 with re-sorting off) on an internal stream the first
  * time it is needed, and launches that graph on the caller's stream for every whole period

@@ -52,6 +52,7 @@ class OracleSim:
         self.E_static = None    # static (gun) field added at the gather, or None
         self.emitter = None     # dict of emitted() arguments and the species, or None
         self.Q_born = np.zeros(self.mesh.N0)   # charge of emitted particles, per node
+        self.sigma_e = self.sigma_m = None      # absorbing layer conductivities, or None
 
     def create(self, dt, bz=0.0):
         if dt > self.dt_max:
@@ -104,9 +105,28 @@ class OracleSim:
         self.inject(z, r, ur, up, uz, em["q"], em["mass"], em["weight"])
         self.Q_born += self.Q - q0
 
+    def set_loss(self, sigma_e, sigma_m):
+        """Absorbing layer: electric conductivity per edge, magnetic per face.  The
+        conduction terms of the two curl equations are time-centred, so with
+        s = sigma dt / (2 eps0) (resp. sigma_m dt / (2 mu0)) each update becomes
+        x <- (1 - s)/(1 + s) x + (lossless increment) / (1 + s)."""
+        if sigma_e is None and sigma_m is None:
+            self.sigma_e = self.sigma_m = None
+            return
+        m = self.mesh
+        self.sigma_e = np.zeros(m.N1) if sigma_e is None else np.array(sigma_e, float)
+        self.sigma_m = np.zeros(m.N2) if sigma_m is None else np.array(sigma_m, float)
+
+    def _loss_factors(self, s):
+        return (1.0 - s) / (1.0 + s), 1.0 / (1.0 + s)
+
     def field_b_half(self):
-        """Eq. full_d_dfl."""
-        return self.B - self.dt * (self.mesh.Dcurl @ self.E)
+        """Eq. full_d_dfl (with the magnetic conduction term in a lossy layer)."""
+        inc = -self.dt * (self.mesh.Dcurl @ self.E)
+        if self.sigma_m is None:
+            return self.B + inc
+        a, b = self._loss_factors(self.sigma_m * self.dt / (2.0 * self.mu0))
+        return a * self.B + b * inc
 
     def push_particles(self, B_half):
         m = self.mesh
@@ -126,7 +146,12 @@ class OracleSim:
         f = m.free
         r = m.Dcurl.T @ (self.mu_inv * B_half) - self.J
         self.D[f] += self.dt * r[f]
-        self.E[f] += self.dt * (self.M @ r[f])
+        inc = self.dt * (self.M @ r[f])
+        if self.sigma_e is None:
+            self.E[f] += inc
+        else:
+            a, b = self._loss_factors(self.sigma_e[f] * self.dt / (2.0 * self.eps0))
+            self.E[f] = a * self.E[f] + b * inc
 
     def step(self, n=1):
         for _ in range(n):
@@ -151,6 +176,12 @@ class OracleSim:
         f = m.free
         res = m.Ddiv[:, f] @ self.D[f] - (self.Q - self.Q_born)
         res[m.node_on_pec] = 0.0
+        if self.sigma_e is not None:
+            # conduction moves charge in a lossy layer: its nodes are left out
+            lossy = np.zeros(m.N0, bool)
+            lossy[m.edge_nodes[self.sigma_e > 0].ravel()] = True
+            lossy[m.tris[self.sigma_m > 0].ravel()] = True
+            res[lossy] = 0.0
         return res
 
     def field_energy(self):

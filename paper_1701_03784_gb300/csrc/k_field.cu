@@ -10,7 +10,8 @@ namespace pic {
 // field coefficients: E(lambda) = sum_k E_k (lambda_a grad lambda_b - lambda_b grad
 // lambda_a) = sum_m lambda_m c_m (E_k plus the static field's edge value when one is set:
 // it drives the particles but takes no part in the leapfrog), and
-// B_phi = (B^{n+1/2} + B^{n-1/2}) / (2A) (W2 = 1/A).
+// B_phi = (B^{n+1/2} + B^{n-1/2}) / (2A) (W2 = 1/A).  In a lossy layer
+// B^{n+1/2} = a_f B^{n-1/2} - b_f dt (D_curl E^n)_f.
 // The same launch clears the step's accumulators (J per edge, Q_abs per node, and in the
 // FP64 build Q^{n+1}, which the particle kernel accumulates).
 template <class P>
@@ -53,7 +54,11 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
             curl += fwd ? E3[k] : -E3[k];
         }
         const float Bold = a.B[f];
-        const float Bnew = Bold - a.dt * curl;
+        float Bnew = Bold - a.dt * curl;
+        if (a.loss_f) {
+            const float2 lf = reinterpret_cast<const float2 *>(a.loss_f)[f];
+            Bnew = lf.x * Bold - lf.y * (a.dt * curl);
+        }
         a.B[f] = Bnew;
         R4[2] = make_float4(c[0][0], c[0][1], c[1][0], c[1][1]);
         R4[3] = make_float4(c[2][0], c[2][1], 0.5f * (Bnew + Bold) * RH.w, 0.f);
@@ -78,7 +83,8 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
         curl += fwd ? Ed : -Ed;
     }
     R Bold = a.B[f];
-    R Bnew = Bold - a.dt * curl;
+    R Bnew = a.loss_f ? a.loss_f[2 * f] * Bold - a.loss_f[2 * f + 1] * (a.dt * curl)
+                      : Bold - a.dt * curl;
     a.B[f] = Bnew;
     rc.bphi = R(0.5) * (Bnew + Bold) * rc.inv_area;
 #pragma unroll
@@ -134,7 +140,8 @@ __global__ void __launch_bounds__(512) k_field_r(FieldArgs<P> a) {
     a.r[i] = (R)r;
 }
 
-// K4b, sliced ELL SpMV over free edges: E_e += dt (M r)_i.  A warp owns a slice of 32 rows
+// K4b, sliced ELL SpMV over free edges: E_e += dt (M r)_i (in a lossy layer
+// E_e <- a_e E_e + b_e dt (M r)_i, a = (1 - s)/(1 + s), b = 1/(1 + s), s = sigma dt/(2 eps0)).  A warp owns a slice of 32 rows
 // stored column-major, so each step of the row loop reads 32 consecutive values.
 template <class P>
 __global__ void __launch_bounds__(512) k_field_spmv(FieldArgs<P> a) {
@@ -152,7 +159,11 @@ __global__ void __launch_bounds__(512) k_field_spmv(FieldArgs<P> a) {
         int32_t col = a.ell_col[idx];
         acc += a.ell_val[idx] * a.r[col];
     }
-    if (row < a.nf) a.E[a.free_edges[row]] += a.dt * acc;
+    if (row < a.nf) {
+        const int32_t e = a.free_edges[row];
+        if (a.loss_e) a.E[e] = a.loss_e[2 * row] * a.E[e] + a.loss_e[2 * row + 1] * (a.dt * acc);
+        else a.E[e] += a.dt * acc;
+    }
 }
 
 template <class P>

@@ -252,6 +252,10 @@ struct FieldArgs {
     TriRec<typename P::R> *rec;
     typename P::R *E;           // N1
     const typename P::R *Es;    // N1 static field added at the gather only, or null
+    // lossy (absorbing) layer, or null: per free-edge row (a, b) with
+    // E <- a E + b dt (M r), per face (a, b) with B <- a B - b dt (D_curl E)
+    const typename P::R *loss_e;  // nf x 2
+    const typename P::R *loss_f;  // N2 x 2
     typename P::R *B;           // N2, B^{n-1/2} in, B^{n+1/2} out
     const typename P::R *mu_inv;// N2
     const int32_t *edge_face;   // nf x 2, per free edge: (face+1) * sign, 0 if none

@@ -73,6 +73,7 @@ struct SimBase {
     virtual pic_status charges_static(double *Q, double *Qp, double *Qa, cudaStream_t s) = 0;
     virtual pic_status set_static_field(const double *E, cudaStream_t s) = 0;
     virtual pic_status set_emitter(const pic_emitter *e, cudaStream_t s) = 0;
+    virtual pic_status set_loss(const double *sig_e, const double *sig_m, cudaStream_t s) = 0;
     int32_t sort_interval = 16;
     int32_t pusher = PIC_PUSHER_BORIS;
     int device = 0;
@@ -118,6 +119,12 @@ struct SimImpl final : SimBase {
     int32_t *el_tri = nullptr;
     int64_t el_room = 0;
     int src_version = 0;
+    // lossy layer: per free edge and per face (a, b) update factors, and the Gauss-law
+    // node mask with the layer's nodes added (conduction moves charge there)
+    R *loss_e = nullptr, *loss_f = nullptr;
+    bool loss_on = false;
+    const uint8_t *pec_mask = nullptr;
+    uint8_t *dgl_mask = nullptr;
 
     bool timing_on = false;
     // host round trips (step_host): uploads and downloads run on streams of their own,
@@ -323,6 +330,7 @@ struct SimImpl final : SimBase {
             (st = upload(ei_, mesh.eps_idx)) || (st = upload(ev_, mesh.eps_val)))
             return st;
         dd = DiagDev{np_, ne_, ns_, pec_, ep_, ei_, ev_, mesh.N0, mesh.N1, mesh.N2};
+        pec_mask = pec_;
         if ((st = dalloc(dgl_ref, mesh.N0)) || (st = dalloc(diag_out, 8))) return st;
         PIC_CUDA_TRY(cudaDeviceSynchronize());
         return PIC_OK;
@@ -362,7 +370,58 @@ struct SimImpl final : SimBase {
         a.N0 = m->N0;
         a.block = tune_block;
         a.Es = static_on ? Es : nullptr;
+        a.loss_e = loss_on ? loss_e : nullptr;
+        a.loss_f = loss_on ? loss_f : nullptr;
         return a;
+    }
+
+    pic_status set_loss(const double *sig_e, const double *sig_m, cudaStream_t s) override {
+        src_version++;
+        if (!sig_e && !sig_m) {
+            loss_on = false;
+            dd.node_on_pec = pec_mask;
+            dgl_dirty = true;
+            return PIC_OK;
+        }
+        const double eps0 = m->units.eps0, mu0 = m->units.mu0;
+        std::vector<R> le(2 * nf), lf(2 * m->N2);
+        std::vector<uint8_t> mask(m->node_on_pec.begin(), m->node_on_pec.end());
+        for (int64_t i = 0; i < nf; i++) {
+            const int32_t e = m->free_edges[i];
+            const double sg = sig_e ? sig_e[e] : 0.0;
+            if (!(sg >= 0.0) || !std::isfinite(sg)) {
+                set_error("pic_sim_set_loss: edge conductivity %lld negative or not finite", (long long)e);
+                return PIC_ERR_ARG;
+            }
+            const double x = sg * dt / (2.0 * eps0);
+            le[2 * i] = (R)((1.0 - x) / (1.0 + x));
+            le[2 * i + 1] = (R)(1.0 / (1.0 + x));
+            if (sg > 0.0) mask[m->edge_nodes[2 * e]] = mask[m->edge_nodes[2 * e + 1]] = 1;
+        }
+        for (int64_t f = 0; f < m->N2; f++) {
+            const double sg = sig_m ? sig_m[f] : 0.0;
+            if (!(sg >= 0.0) || !std::isfinite(sg)) {
+                set_error("pic_sim_set_loss: face conductivity %lld negative or not finite", (long long)f);
+                return PIC_ERR_ARG;
+            }
+            const double x = sg * dt / (2.0 * mu0);
+            lf[2 * f] = (R)((1.0 - x) / (1.0 + x));
+            lf[2 * f + 1] = (R)(1.0 / (1.0 + x));
+            if (sg > 0.0)
+                for (int k = 0; k < 3; k++) mask[m->tri[3 * f + k]] = 1;
+        }
+        pic_status st;
+        if (!loss_e && ((st = dalloc(loss_e, 2 * nf)) != PIC_OK || (st = dalloc(loss_f, 2 * m->N2)) != PIC_OK ||
+                        (st = dalloc(dgl_mask, m->N0)) != PIC_OK))
+            return st;
+        PIC_CUDA_TRY(cudaMemcpyAsync(loss_e, le.data(), sizeof(R) * 2 * nf, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(loss_f, lf.data(), sizeof(R) * 2 * m->N2, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaMemcpyAsync(dgl_mask, mask.data(), m->N0, cudaMemcpyHostToDevice, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        dd.node_on_pec = dgl_mask;
+        loss_on = true;
+        dgl_dirty = true;   // the reference is taken again over the new node set
+        return PIC_OK;
     }
 
     pic_status set_static_field(const double *Eh, cudaStream_t s) override {
@@ -1244,6 +1303,12 @@ extern "C" pic_status pic_sim_set_static_field(pic_sim *s, const double *E_stati
 extern "C" pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *st) {
     SIM_CHECK(s, "pic_sim_set_emitter");
     return s->impl->set_emitter(e, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_sim_set_loss(pic_sim *s, const double *sigma_e, const double *sigma_m,
+                                       void *st) {
+    SIM_CHECK(s, "pic_sim_set_loss");
+    return s->impl->set_loss(sigma_e, sigma_m, (cudaStream_t)st);
 }
 
 extern "C" pic_status pic_fields_set(pic_sim *s, const double *E, const double *B, void *st) {

@@ -76,6 +76,7 @@ _SIGS = {
     "pic_static_potential": [_P, _I64, _P, _P, _P, _P],
     "pic_sim_set_static_field": [_P, _P, _P],
     "pic_sim_set_emitter": [_P, ctypes.POINTER(pic_emitter), _P],
+    "pic_sim_set_loss": [_P, _P, _P, _P],
     "pic_sim_set_graph": [_P, _I32],
     "pic_sim_autotune": [_P, _I32, _P, _P],
     "pic_mlp_create": [_I32, _I32, _P, _I32, _P],
@@ -325,6 +326,15 @@ def pic_sim_set_emitter(sim, z, rho0, rho1, per_step, u_normal, u_thermal, seed,
     e = pic_emitter(z, rho0, rho1, per_step, u_normal, u_thermal, seed, q, m, w)
     _check(_lib.pic_sim_set_emitter(sim.ptr, ctypes.byref(e), _stream(stream)),
            "pic_sim_set_emitter")
+
+
+def pic_sim_set_loss(sim, sigma_e, sigma_m, stream=None):
+    """Absorbing layer: conductivity per edge (S/m) and magnetic conductivity per face
+    (ohm/m); both None makes the fields lossless again."""
+    se = None if sigma_e is None else _arr(sigma_e, np.float64)
+    sm = None if sigma_m is None else _arr(sigma_m, np.float64)
+    _check(_lib.pic_sim_set_loss(sim.ptr, _ptr(se), _ptr(sm), _stream(stream)),
+           "pic_sim_set_loss")
 
 
 def pic_sim_set_pusher(sim, pusher):
