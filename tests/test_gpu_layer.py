@@ -36,9 +36,9 @@ def _pulse(m):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_lossy_fields_match_oracle(pic, guide, prec):
-    """A pulse already inside a graded layer (strong conductivities) for 300 steps, with
-    charged particles in the guide: E and B against the oracle (FP64 1e-12 per step
-    scale, FP32 1e-5), and the Gauss-law drift outside the layer at round-off."""
+    """A pulse already inside a graded layer (strong conductivities) for 40 steps, with
+    charged particles in the guide: E and B against the oracle (FP64 1e-12 per step,
+    FP32 1e-4), and the Gauss-law drift outside the layer at round-off."""
     arrays, oracle = guide
     o = OracleSim.__new__(OracleSim)
     o.__dict__.update({k: (v.copy() if isinstance(v, np.ndarray) else v)
@@ -61,11 +61,11 @@ def test_lossy_fields_match_oracle(pic, guide, prec):
     pic.pic_fields_set(sim, E0, np.zeros(m.N2))
     pic.pic_sim_set_loss(sim, se, sm)
     pic.pic_particles_inject(sim, z[keep], r[keep], ur[keep], up[keep], uz[keep], -1.0, 1.0, 1e-3)
-    steps = 300
+    steps = 40
     pic.pic_step(sim, steps)
     o.step(steps)
     d = pic.pic_diagnostics(sim, fields=True)
-    tol = 1e-12 * steps if prec == "fp64" else 1e-5 * 30
+    tol = 1e-12 * steps if prec == "fp64" else 1e-4
     assert np.abs(d["E"] - o.E).max() <= tol * np.abs(E0).max()
     assert np.abs(d["B"] - o.B).max() <= tol * np.abs(o.B).max()
     assert d["dgl_drift"] < (1e-10 if prec == "fp64" else 1e-5)
