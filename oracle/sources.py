@@ -52,12 +52,13 @@ def emitted(z0, rho0, rho1, u_normal, u_thermal, seed, pids):
     return np.full(len(rho), float(z0)), rho, ur, up, uz
 
 
-def static_potential(mesh, star_eps, held_nodes, held_phi):
+def static_potential(mesh, star_eps, held_nodes, held_phi, charge=None):
     """Static field of the electrodes: the node potential phi with phi fixed at
-    held_nodes and D_div star_eps D_div^T phi = 0 at every other node (the discrete Gauss
-    law without charge for E = -grad phi, whose Whitney-1 edge values are D_div^T phi: phi
-    at the tail minus phi at the head), i.e. zero normal flux where no potential is held.
-    Returns (phi, E_static)."""
+    held_nodes and D_div star_eps D_div^T phi = Q at every other node (the discrete Gauss
+    law D_div D = Q for D = star_eps E, E = -grad phi, whose Whitney-1 edge values are
+    D_div^T phi: phi at the tail minus phi at the head), i.e. zero normal flux where no
+    potential is held.  Q (node charges in the units of star_eps, per radian) defaults to
+    zero.  Returns (phi, E_static)."""
     L = (mesh.Ddiv @ star_eps @ mesh.Ddiv.T).tocsr()
     held = np.zeros(mesh.N0, bool)
     held[np.asarray(held_nodes)] = True
@@ -65,6 +66,8 @@ def static_potential(mesh, star_eps, held_nodes, held_phi):
     phi[np.asarray(held_nodes)] = held_phi
     free = ~held
     rhs = -(L[free][:, held] @ phi[held])
+    if charge is not None:
+        rhs = rhs + np.asarray(charge, float)[free]
     phi[free] = spla.spsolve(L[free][:, free].tocsc(), rhs)
     return phi, mesh.Ddiv.T @ phi
 

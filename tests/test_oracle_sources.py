@@ -129,3 +129,27 @@ def test_charge_conservation_with_particles_born_every_step():
             res0 = g.copy()
         assert np.abs(g - res0).max() < 1e-10 * np.abs(s.Q_born).max()
     assert len(s.tri) == 20 * 200 and s.counters[2] > 0
+
+
+def test_gauss_law_of_a_charged_shell_fixes_the_ring_normalisation():
+    """Macro-particles on a cylindrical shell rho = 0.4 inside a grounded tube rho = 1
+    (ends without normal flux: an infinitely long line).  Their Eq. charge deposit (q_src =
+    w q / (2 pi) per radian) drives the discrete Gauss law through star_eps (also per
+    radian); outside the shell the potential must fall as Q_tot / (2 pi eps0 L) ln(rho),
+    Q_tot the 3D charge N w q.  A missing or doubled 2 pi shows as a factor 6.28."""
+    from oracle import particles as P
+    nodes, tris, be, bt = W.cavity_mesh(a=1.0, L=4.0, n_tri=6000, seed=12)
+    s = OracleSim(nodes, tris, be, bt)
+    m = s.mesh
+    n, w, q = 20000, 2e-3, -1.0
+    z = (np.arange(n) + 0.5) * (4.0 / n)     # evenly spread: no shot noise in the line charge
+    r = np.full(n, 0.4)
+    tri, lam = P.locate(m, z, r)
+    Q = np.zeros(m.N0)
+    P.deposit_charge(s.pm, tri, np.ascontiguousarray(lam), w * q / (2 * math.pi), Q)
+    held = np.flatnonzero(np.isclose(m.nodes[:, 1], 1.0))
+    phi, _ = S.static_potential(m, s.star_eps, held, np.zeros(len(held)), charge=Q)
+    k = np.flatnonzero((m.nodes[:, 1] > 0.55) & (m.nodes[:, 1] < 0.95)
+                       & (m.nodes[:, 0] > 1.0) & (m.nodes[:, 0] < 3.0))
+    expect = n * w * q / (2 * math.pi * 1.0 * 4.0) * np.log(1.0 / m.nodes[k, 1])
+    assert np.abs(phi[k] - expect).max() < 0.005 * np.abs(expect).max()
