@@ -181,14 +181,17 @@ pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher);
 
 /* Sources either side of the particle loop (Secs. 5.2, 5.3).
  *
- * The static (gun) field of the electrodes: the node potential phi with phi held at
- * held_nodes (n_held of them, potentials held_phi) and D_div star_eps D_div^T phi = 0 at
- * every other node, i.e. the discrete Gauss law without charge for E = -grad phi, whose
- * Whitney-1 edge values are phi(tail) - phi(head) (zero normal flux where no potential is
- * held).  Solved on the host by conjugate gradients; phi_out (N0) and E_out (N1) may each
- * be NULL.  Errors: ARG, MESH (a part of the mesh reaches no held node). */
+ * The static (gun) field of the electrodes, by Poisson's equation (Sec. 5.3): the node
+ * potential phi with phi held at held_nodes (n_held of them, potentials held_phi) and
+ * D_div star_eps D_div^T phi = Q at every other node, i.e. the discrete Gauss law for
+ * E = -grad phi, whose Whitney-1 edge values are phi(tail) - phi(head) (zero normal flux
+ * where no potential is held).  charge: node charges Q (N0, per radian like star_eps:
+ * w q / (2 pi) per unit barycentric weight), or NULL for none.  Solved on the host by
+ * conjugate gradients; phi_out (N0) and E_out (N1) may each be NULL.  Errors: ARG, MESH
+ * (a part of the mesh reaches no held node). */
 pic_status pic_static_potential(const pic_mesh *m, int64_t n_held, const int32_t *held_nodes,
-                                const double *held_phi, double *phi_out, double *E_out);
+                                const double *held_phi, const double *charge, double *phi_out,
+                                double *E_out);
 
 /* A static field (N1 edge values, e.g. E_out above) added to E^n at the gather only: it
  * drives the particles but takes no part in the leapfrog (the electrodes' voltage is held

@@ -8,14 +8,14 @@
 namespace pic {
 
 // The static potential's system: for E = -grad phi, whose Whitney-1 edge values are
-// phi(tail) - phi(head), the discrete Gauss law without charge reads
-// D_div star_eps D_div^T phi = 0.  Because grad maps the Whitney-0 hats onto Whitney-1
+// phi(tail) - phi(head), the discrete Gauss law reads D_div star_eps D_div^T phi = Q (zero
+// without space charge).  Because grad maps the Whitney-0 hats onto Whitney-1
 // forms exactly, that matrix is the rho-weighted stiffness eps0 int rho grad(l_k).grad(l_l)
 // over each triangle (rho linear: its mean times the area), assembled here per triangle.
 // Held nodes keep their potential; the others solve the system (conjugate gradients,
 // Jacobi preconditioner, relative residual 1e-13).
 static pic_status solve_static(const HostMesh &m, const std::vector<uint8_t> &held,
-                               std::vector<double> &phi) {
+                               const double *charge, std::vector<double> &phi) {
     const int64_t N0 = m.N0;
     std::vector<std::vector<std::pair<int32_t, double>>> rows(N0);
     for (int64_t t = 0; t < m.N2; t++) {
@@ -53,11 +53,11 @@ static pic_status solve_static(const HostMesh &m, const std::vector<uint8_t> &he
             y[k] = s;
         }
     };
-    // right-hand side: minus the held potentials' coupling
+    // right-hand side: the node charge minus the held potentials' coupling
     std::vector<double> b(N0, 0.0), diag(N0, 1.0);
     for (int64_t k = 0; k < N0; k++) {
         if (held[k]) continue;
-        double s = 0.0;
+        double s = charge ? charge[k] : 0.0;
         for (int64_t q = ptr[k]; q < ptr[k + 1]; q++) {
             if (held[idx[q]]) s -= val[q] * phi[idx[q]];
             if (idx[q] == k) diag[k] = val[q];
@@ -198,7 +198,8 @@ using namespace pic;
 
 extern "C" pic_status pic_static_potential(const pic_mesh *pm, int64_t n_held,
                                            const int32_t *held_nodes, const double *held_phi,
-                                           double *phi_out, double *E_out) {
+                                           const double *charge, double *phi_out,
+                                           double *E_out) {
     if (!pm || n_held <= 0 || !held_nodes || !held_phi) {
         set_error("pic_static_potential: bad argument");
         return PIC_ERR_ARG;
@@ -215,7 +216,13 @@ extern "C" pic_status pic_static_potential(const pic_mesh *pm, int64_t n_held,
         held[n] = 1;
         phi[n] = held_phi[k];
     }
-    pic_status st = solve_static(m, held, phi);
+    if (charge)
+        for (int64_t k = 0; k < m.N0; k++)
+            if (!std::isfinite(charge[k])) {
+                set_error("pic_static_potential: node charge %lld is not finite", (long long)k);
+                return PIC_ERR_ARG;
+            }
+    pic_status st = solve_static(m, held, charge, phi);
     if (st != PIC_OK) return st;
     if (phi_out) std::copy(phi.begin(), phi.end(), phi_out);
     if (E_out)

@@ -73,7 +73,7 @@ _SIGS = {
     "pic_sim_create": [_P, _D, _D, _I64, _P],
     "pic_sim_set_sort_interval": [_P, _I32],
     "pic_sim_set_pusher": [_P, _I32],
-    "pic_static_potential": [_P, _I64, _P, _P, _P, _P],
+    "pic_static_potential": [_P, _I64, _P, _P, _P, _P, _P],
     "pic_sim_set_static_field": [_P, _P, _P],
     "pic_sim_set_emitter": [_P, ctypes.POINTER(pic_emitter), _P],
     "pic_sim_set_loss": [_P, _P, _P, _P],
@@ -296,16 +296,18 @@ def pic_sim_set_sort_interval(sim, interval):
     _check(_lib.pic_sim_set_sort_interval(sim.ptr, interval), "pic_sim_set_sort_interval")
 
 
-def pic_static_potential(mesh, held_nodes, held_phi):
-    """(phi on nodes, E_static on edges) of the electrodes: phi held at held_nodes,
-    discrete Laplace problem elsewhere (Sec. 5.3)."""
+def pic_static_potential(mesh, held_nodes, held_phi, charge=None):
+    """(phi on nodes, E_static on edges): phi held at held_nodes, discrete Poisson problem
+    with the node charges (per radian; None: none) elsewhere (Sec. 5.3)."""
     held_nodes = _arr(held_nodes, np.int32)
     held_phi = _arr(np.broadcast_to(held_phi, held_nodes.shape), np.float64)
+    Q = None if charge is None else _arr(charge, np.float64)
     info = pic_mesh_info(mesh)
     phi = np.zeros(info["n_nodes"])
     E = np.zeros(info["n_edges"])
     _check(_lib.pic_static_potential(mesh.ptr, len(held_nodes), _ptr(held_nodes),
-                                     _ptr(held_phi), _ptr(phi), _ptr(E)), "pic_static_potential")
+                                     _ptr(held_phi), _ptr(Q), _ptr(phi), _ptr(E)),
+           "pic_static_potential")
     return phi, E
 
 

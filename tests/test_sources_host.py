@@ -16,7 +16,7 @@ def pic():
     return p
 
 
-@pytest.mark.parametrize("case", ["planar", "quadrupole", "diode_si"])
+@pytest.mark.parametrize("case", ["planar", "quadrupole", "diode_si", "charged"])
 def test_static_potential_matches_oracle(pic, case):
     if case == "diode_si":
         nodes, tris, be, bt = W.diode_mesh(n_tri=3000, seed=8)
@@ -32,9 +32,12 @@ def test_static_potential_matches_oracle(pic, case):
         z = om.nodes[:, 0]
         held = np.flatnonzero((z == z.min()) | (z == z.max()))
         vals = np.where(om.nodes[held, 0] == z.min(), 0.0, 1e5)
-    phi_o, E_o = S.static_potential(om, hodge_eps(om, eps0), held, vals)
+    Q = None
+    if case == "charged":
+        Q = np.random.default_rng(4).normal(size=om.N0) * 0.1
+    phi_o, E_o = S.static_potential(om, hodge_eps(om, eps0), held, vals, charge=Q)
     m = pic.pic_mesh_create(nodes, tris, be, bt, eps0=eps0, mu0=1.0 if eps0 == 1.0 else 1.25663706212e-6)
-    phi, E = pic.pic_static_potential(m, held, vals)
+    phi, E = pic.pic_static_potential(m, held, vals, charge=Q)
     scale = np.abs(phi_o).max()
     assert np.abs(phi - phi_o).max() <= 1e-9 * scale
     assert np.abs(E - E_o).max() <= 1e-9 * scale
