@@ -529,6 +529,33 @@ def run_spai_sweep(args):
     return 0
 
 
+def run_staircase(args):
+    """Staircasing study (Sec. 5.3) on one slow-wave-structure period: the 0- and
+    pi-point frequencies from cold tests on conformal and staircased meshes of the same
+    spacing, against the finest conformal mesh."""
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    from paper_1701_03784_gb300 import coldtest
+    rows = []
+    t0 = time.perf_counter()
+    for stair in (False, True):
+        for n in (500, 1000, 2000, 4000, 8000):
+            f0, fpi, nt = coldtest.ring_down(n, stair)
+            rows.append({"staircase": stair, "triangles": nt, "f0_GHz": f0 / 1e9,
+                         "fpi_GHz": fpi / 1e9})
+    ref = [r for r in rows if not r["staircase"]][-1]
+    for r in rows:
+        r["f0_rel_err"] = r["f0_GHz"] / ref["f0_GHz"] - 1.0
+        r["fpi_rel_err"] = r["fpi_GHz"] / ref["fpi_GHz"] - 1.0
+    print(json.dumps({"metric": "staircasing: cold-test frequency error of one SWS period",
+                      "unit": "relative", "rows": rows,
+                      "wall_s": time.perf_counter() - t0,
+                      "config": {"workload": "one period (7.5 mm) of R(z) = 15 + 2.1 cos(2 pi z "
+                                             "/ 7.5 mm) mm between ripple maxima, FP64, 1.5 ns "
+                                             "ring-down, reference: the finest conformal mesh"}}))
+    return 0
+
+
 def run_diode(args):
     """Planar diode at 100 kV over 1 cm with a 6 cm emitter (Sec. 5.2's check on a planar
     gap): the largest injection that forms no virtual cathode (no particle returns to the
@@ -584,6 +611,8 @@ def main():
                     help="time surrogate-network inference on this many queries instead")
     ap.add_argument("--spai-sweep", action="store_true",
                     help="SPAI pattern / drop-tolerance sweep (accuracy and cost) instead")
+    ap.add_argument("--staircase", action="store_true",
+                    help="staircasing study: cold tests of one SWS period instead")
     ap.add_argument("--diode", action="store_true",
                     help="planar space-charge-limited diode (static field + emission) instead")
     ap.add_argument("--no-tune", action="store_true",
@@ -603,6 +632,8 @@ def main():
         return run_spai_sweep(args)
     if args.diode:
         return run_diode(args)
+    if args.staircase:
+        return run_staircase(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

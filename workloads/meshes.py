@@ -36,12 +36,26 @@ def _segment_points(a, b, h):
     return np.linspace(a, b, n + 1)
 
 
+def _polyline_points(corners, h):
+    """Points along a polyline (corners included) at spacing close to h per segment."""
+    out = [corners[:1]]
+    for a, b in zip(corners[:-1], corners[1:]):
+        n = max(1, int(round(np.hypot(*(b - a)) / h)))
+        t = np.linspace(0.0, 1.0, n + 1)[1:, None]
+        out.append(a + t * (b - a))
+    return np.concatenate(out, 0)
+
+
 def jittered_delaunay(z0, z1, R, n_tri, seed, jitter=0.2,
-                      end_tags=(BC_PEC, BC_PEC), wall_tag=BC_PEC, breaks=(), wall_refine=1.0):
+                      end_tags=(BC_PEC, BC_PEC), wall_tag=BC_PEC, breaks=(), wall_refine=1.0,
+                      wall_corners=None):
     """Mesh of {z0<=z<=z1, 0<=rho<=R(z)} with about ``n_tri`` triangles.
 
     ``wall_refine`` < 1 places the wall points closer than the interior spacing (for
-    walls whose curvature a coarse mesh does not resolve).
+    walls whose curvature a coarse mesh does not resolve).  ``wall_corners`` (an array of
+    (z, rho) corners from (z0, R(z0)) to (z1, R(z1))) lays the wall on that polyline
+    instead of sampling the curve, e.g. a staircase with vertical steps (R must then give
+    the larger radius exactly at a step).
     Returns (nodes, tris, bedges, btags); see the package docstring for layouts.
     """
     rng = np.random.default_rng(seed)
@@ -60,8 +74,11 @@ def jittered_delaunay(z0, z1, R, n_tri, seed, jitter=0.2,
         re = _segment_points(0.0, float(R(np.array([ze]))[0]), h)[1:]
         pts.append(np.stack([np.full_like(re, ze), re], 1))
     # wall (corners excluded: they belong to the end planes)
-    zw, rw = _wall_points(R, z0, z1, h * wall_refine, breaks)
-    pts.append(np.stack([zw[1:-1], rw[1:-1]], 1))
+    if wall_corners is None:
+        zw, rw = _wall_points(R, z0, z1, h * wall_refine, breaks)
+        pts.append(np.stack([zw[1:-1], rw[1:-1]], 1))
+    else:
+        pts.append(_polyline_points(np.asarray(wall_corners, float), h * wall_refine)[1:-1])
     n_boundary = sum(len(p) for p in pts)
 
     # interior jittered triangular lattice
@@ -81,8 +98,12 @@ def jittered_delaunay(z0, z1, R, n_tri, seed, jitter=0.2,
     keep = ((gz > z0 + margin) & (gz < z1 - margin) & (gr > margin)
             & (gr < R(np.clip(gz, z0, z1)) - margin * 0.5))
     # distance to the wall measured along the normal (dense wall sampling)
-    zd = np.linspace(z0, z1, int(40 * (z1 - z0) / h) + 2)
-    dist, _ = cKDTree(np.stack([zd, R(zd)], 1)).query(np.stack([gz, gr], 1))
+    if wall_corners is None:
+        zd = np.linspace(z0, z1, int(40 * (z1 - z0) / h) + 2)
+        dense = np.stack([zd, R(zd)], 1)
+    else:
+        dense = _polyline_points(np.asarray(wall_corners, float), h / 40.0)
+    dist, _ = cKDTree(dense).query(np.stack([gz, gr], 1))
     keep &= dist > margin
     pts.append(np.stack([gz[keep], gr[keep]], 1))
     P = np.concatenate(pts, 0)
@@ -189,6 +210,48 @@ def bwo_small_mesh(n_tri=3000, seed=1012):
 def diode_mesh(n_tri=20_000, seed=1001, gap=1e-2, radius=2e-2):
     """Planar diode: cathode plane z=0, anode plane z=gap, outer wall at rho=radius."""
     return rect_mesh(gap, radius, n_tri, seed)
+
+
+def sws_cell_mesh(n_tri, seed=1020, staircase=False, r0=15.0e-3, ripple=2.1e-3,
+                  period=7.5e-3):
+    """One period of a rippled slow-wave structure between two ripple maxima,
+    R(z) = r0 + ripple cos(2 pi z / period) for z in [0, period], conducting end planes
+    (the symmetry planes: the cell's TM01 resonances are the 0 and pi points of the
+    periodic structure's dispersion).  staircase=True replaces the wall by steps of the
+    mesh spacing h in both z and rho (each z-bin at R of its centre rounded to h): the
+    boundary a structured mesh of that spacing would see."""
+    def R(z):
+        return r0 + ripple * np.cos(2.0 * np.pi * np.asarray(z, float) / period)
+
+    if not staircase:
+        for refine in (0.7, 0.5, 0.35, 0.25):
+            try:
+                return jittered_delaunay(0.0, period, R, n_tri, seed, wall_refine=refine)
+            except RuntimeError:
+                continue
+        raise RuntimeError("sws_cell_mesh: no conforming mesh")
+    zz = np.linspace(0.0, period, 20001)
+    area = float(np.sum(0.5 * (R(zz)[1:] + R(zz)[:-1]) * np.diff(zz)))
+    h = np.sqrt(4.0 * area / (np.sqrt(3.0) * n_tri))
+    nb = max(2, int(round(period / h)))
+    edges = np.linspace(0.0, period, nb + 1)
+    level = np.maximum(np.round(R(0.5 * (edges[:-1] + edges[1:])) / h), 1.0) * h
+    corners = [(0.0, level[0])]
+    for k in range(nb):
+        corners.append((edges[k + 1], level[k]))
+        if k + 1 < nb and level[k + 1] != level[k]:
+            corners.append((edges[k + 1], level[k + 1]))
+
+    def Rs(z):
+        z = np.asarray(z, float)
+        k = np.clip(np.searchsorted(edges, z, side="right") - 1, 0, nb - 1)
+        r = level[k]
+        # at a step the larger of the two radii (the step's edge belongs to the domain)
+        at = np.isclose(z, edges[np.clip(k, 0, nb)]) & (k > 0)
+        return np.where(at, np.maximum(r, level[np.maximum(k - 1, 0)]), r)
+
+    return jittered_delaunay(0.0, period, Rs, n_tri, seed, wall_refine=0.7,
+                             wall_corners=np.array(corners))
 
 
 def two_triangle_mesh():
