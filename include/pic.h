@@ -235,6 +235,25 @@ pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *cuda_stre
 pic_status pic_sim_set_loss(pic_sim *s, const double *sigma_e, const double *sigma_m,
                             void *cuda_stream);
 
+/* Field probes recorded on the device (the output-port signal of Sec. 5.3, field energy
+ * envelopes): n_entries (face, group, weight) triples; after the B update of a step,
+ * group g sums weight * B_f (power[g] = 1) or weight * B_f^2 (power[g] = 2) over its
+ * entries, B being B^{n+1/2}.  Every `every` steps, counted from this call, the n_groups
+ * sums are appended to a device buffer of `capacity` records; nothing else waits for the
+ * host.  n_entries = 0 removes the probes.  Device memory of earlier probe sets is held
+ * until the simulation is destroyed.  Errors: ARG, OOM, CUDA.  Not an operation of the
+ * paper. */
+pic_status pic_sim_set_probes(pic_sim *s, int64_t n_entries, const int32_t *face,
+                              const int32_t *group, const double *weight, int32_t n_groups,
+                              const int32_t *power, int64_t capacity, int32_t every,
+                              void *cuda_stream);
+
+/* Copy out the records made since the last read (at most cap_records x n_groups doubles,
+ * record-major) and start a new set; *n_dropped counts records that found the buffer full
+ * or did not fit cap_records.  Synchronous.  Errors: STATE (no probes), CUDA. */
+pic_status pic_probes_read(pic_sim *s, double *out, int64_t cap_records, int64_t *n_records,
+                           int64_t *n_dropped, void *cuda_stream);
+
 /* Replay steps from a CUDA graph (off by default).  pic_step then records one period of
  * 2 x the re-sort interval steps (2 with re-sorting off) on an internal stream the first
  * time it is needed, and launches that graph on the caller's stream for every whole period

@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic_gb300.so")
 SOURCES = ["mesh.cpp", "spai.cpp", "sources.cpp", "sim.cu", "k_push.cu", "k_push_f32.cu", "k_field.cu",
-           "k_sort.cu", "k_diag.cu", "k_emit.cu", "mlp.cu", "k_mlp_tc.cu"]
+           "k_sort.cu", "k_diag.cu", "k_emit.cu", "k_probe.cu", "mlp.cu", "k_mlp_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -247,6 +247,25 @@ struct EmitArgs {
 template <class P>
 void launch_emit(const EmitArgs<P> &a, cudaStream_t s);
 
+// field probes: group g owns entries [ptr[g], ptr[g+1]) of (face, weight); state[0] is
+// the step phase, state[1] the records written, state[2] the records dropped
+template <class P>
+struct ProbeArgs {
+    const typename P::R *B;
+    const int64_t *ptr;
+    const int32_t *face;
+    const double *weight;
+    const int32_t *power;
+    double *buf;            // capacity x n_groups
+    long long *state;
+    unsigned *done;
+    int32_t n_groups, every;
+    long long capacity;
+};
+
+template <class P>
+void launch_probe(const ProbeArgs<P> &a, cudaStream_t s);
+
 template <class P>
 struct FieldArgs {
     TriRec<typename P::R> *rec;

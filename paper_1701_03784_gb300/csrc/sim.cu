@@ -74,6 +74,11 @@ struct SimBase {
     virtual pic_status set_static_field(const double *E, cudaStream_t s) = 0;
     virtual pic_status set_emitter(const pic_emitter *e, cudaStream_t s) = 0;
     virtual pic_status set_loss(const double *sig_e, const double *sig_m, cudaStream_t s) = 0;
+    virtual pic_status set_probes(int64_t n, const int32_t *face, const int32_t *group,
+                                  const double *weight, int32_t n_groups, const int32_t *power,
+                                  int64_t capacity, int32_t every, cudaStream_t s) = 0;
+    virtual pic_status probes_read(double *out, int64_t cap, int64_t *n_rec, int64_t *n_drop,
+                                   cudaStream_t s) = 0;
     int32_t sort_interval = 16;
     int32_t pusher = PIC_PUSHER_BORIS;
     int device = 0;
@@ -125,6 +130,9 @@ struct SimImpl final : SimBase {
     bool loss_on = false;
     const uint8_t *pec_mask = nullptr;
     uint8_t *dgl_mask = nullptr;
+    // field probes recorded on the device
+    ProbeArgs<P> probe{};
+    bool probes_on = false;
 
     bool timing_on = false;
     // host round trips (step_host): uploads and downloads run on streams of their own,
@@ -373,6 +381,83 @@ struct SimImpl final : SimBase {
         a.loss_e = loss_on ? loss_e : nullptr;
         a.loss_f = loss_on ? loss_f : nullptr;
         return a;
+    }
+
+    pic_status set_probes(int64_t n, const int32_t *face, const int32_t *group, const double *weight,
+                          int32_t n_groups, const int32_t *power, int64_t capacity, int32_t every,
+                          cudaStream_t s) override {
+        src_version++;
+        if (n <= 0 || n_groups <= 0) {
+            probes_on = false;
+            return PIC_OK;
+        }
+        if (!face || !group || !weight || !power || capacity < 1 || every < 1) {
+            set_error("pic_sim_set_probes: bad argument");
+            return PIC_ERR_ARG;
+        }
+        std::vector<int64_t> ptr(n_groups + 1, 0);
+        for (int64_t k = 0; k < n; k++) {
+            if (face[k] < 0 || face[k] >= m->N2 || group[k] < 0 || group[k] >= n_groups ||
+                !std::isfinite(weight[k])) {
+                set_error("pic_sim_set_probes: entry %lld out of range", (long long)k);
+                return PIC_ERR_ARG;
+            }
+            ptr[group[k] + 1]++;
+        }
+        for (int32_t g = 0; g < n_groups; g++) {
+            if (power[g] != 1 && power[g] != 2) {
+                set_error("pic_sim_set_probes: power of group %d is not 1 or 2", (int)g);
+                return PIC_ERR_ARG;
+            }
+            ptr[g + 1] += ptr[g];
+        }
+        std::vector<int32_t> f(n);
+        std::vector<double> w(n);
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t k = 0; k < n; k++) {
+            const int64_t at = fill[group[k]]++;
+            f[at] = face[k];
+            w[at] = weight[k];
+        }
+        std::vector<int32_t> pw(power, power + n_groups);
+        int64_t *d_ptr;
+        int32_t *d_face, *d_pow;
+        double *d_w, *d_buf;
+        long long *d_state;
+        unsigned *d_done;
+        pic_status st;
+        if ((st = upload(d_ptr, ptr)) || (st = upload(d_face, f)) || (st = upload(d_w, w)) ||
+            (st = upload(d_pow, pw)) || (st = dalloc(d_buf, capacity * (int64_t)n_groups)) ||
+            (st = dalloc(d_state, 3)) || (st = dalloc(d_done, 1)))
+            return st;
+        PIC_CUDA_TRY(cudaMemsetAsync(d_state, 0, 3 * sizeof(long long), s));
+        PIC_CUDA_TRY(cudaMemsetAsync(d_done, 0, sizeof(unsigned), s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        probe = ProbeArgs<P>{B, d_ptr, d_face, d_w, d_pow, d_buf, d_state, d_done, n_groups, every,
+                             (long long)capacity};
+        probes_on = true;
+        return PIC_OK;
+    }
+
+    pic_status probes_read(double *out, int64_t cap_rec, int64_t *n_rec, int64_t *n_drop,
+                           cudaStream_t s) override {
+        if (!probes_on) {
+            set_error("pic_probes_read: no probes set");
+            return PIC_ERR_STATE;
+        }
+        long long st3[3];
+        PIC_CUDA_TRY(cudaMemcpyAsync(st3, probe.state, sizeof st3, cudaMemcpyDeviceToHost, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        const int64_t rec = std::min<int64_t>(st3[1], cap_rec);
+        if (out && rec > 0)
+            PIC_CUDA_TRY(cudaMemcpyAsync(out, probe.buf, sizeof(double) * rec * probe.n_groups,
+                                         cudaMemcpyDeviceToHost, s));
+        // the records are consumed; the step phase carries on
+        PIC_CUDA_TRY(cudaMemsetAsync(probe.state + 1, 0, 2 * sizeof(long long), s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (n_rec) *n_rec = rec;
+        if (n_drop) *n_drop = st3[2] + (st3[1] - rec);
+        return PIC_OK;
     }
 
     pic_status set_loss(const double *sig_e, const double *sig_m, cudaStream_t s) override {
@@ -830,6 +915,7 @@ struct SimImpl final : SimBase {
             fa.Qn = Qn();
             fa.Qnext = Qnext;
             launch_field_b<P>(fa, s);
+            if (probes_on) launch_probe<P>(probe, s);
             PushArgs<P> pa;
             pa.rec = rec;
             pa.p = parts[cur];
@@ -1309,6 +1395,21 @@ extern "C" pic_status pic_sim_set_loss(pic_sim *s, const double *sigma_e, const 
                                        void *st) {
     SIM_CHECK(s, "pic_sim_set_loss");
     return s->impl->set_loss(sigma_e, sigma_m, (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_sim_set_probes(pic_sim *s, int64_t n_entries, const int32_t *face,
+                                         const int32_t *group, const double *weight,
+                                         int32_t n_groups, const int32_t *power,
+                                         int64_t capacity, int32_t every, void *st) {
+    SIM_CHECK(s, "pic_sim_set_probes");
+    return s->impl->set_probes(n_entries, face, group, weight, n_groups, power, capacity, every,
+                               (cudaStream_t)st);
+}
+
+extern "C" pic_status pic_probes_read(pic_sim *s, double *out, int64_t cap_records,
+                                      int64_t *n_records, int64_t *n_dropped, void *st) {
+    SIM_CHECK(s, "pic_probes_read");
+    return s->impl->probes_read(out, cap_records, n_records, n_dropped, (cudaStream_t)st);
 }
 
 extern "C" pic_status pic_fields_set(pic_sim *s, const double *E, const double *B, void *st) {

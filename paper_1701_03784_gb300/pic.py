@@ -77,6 +77,8 @@ _SIGS = {
     "pic_sim_set_static_field": [_P, _P, _P],
     "pic_sim_set_emitter": [_P, ctypes.POINTER(pic_emitter), _P],
     "pic_sim_set_loss": [_P, _P, _P, _P],
+    "pic_sim_set_probes": [_P, _I64, _P, _P, _P, _I32, _P, _I64, _I32, _P],
+    "pic_probes_read": [_P, _P, _I64, _P, _P, _P],
     "pic_sim_set_graph": [_P, _I32],
     "pic_sim_autotune": [_P, _I32, _P, _P],
     "pic_mlp_create": [_I32, _I32, _P, _I32, _P],
@@ -337,6 +339,29 @@ def pic_sim_set_loss(sim, sigma_e, sigma_m, stream=None):
     sm = None if sigma_m is None else _arr(sigma_m, np.float64)
     _check(_lib.pic_sim_set_loss(sim.ptr, _ptr(se), _ptr(sm), _stream(stream)),
            "pic_sim_set_loss")
+
+
+def pic_sim_set_probes(sim, face, group, weight, power, capacity, every, stream=None):
+    """Device-recorded field sums (see pic.h); face/group/weight per entry, power per
+    group (1: sum w B, 2: sum w B^2).  Empty face removes the probes."""
+    face = _arr(face, np.int32)
+    group = _arr(group, np.int32)
+    weight = _arr(weight, np.float64)
+    power = _arr(power, np.int32)
+    _check(_lib.pic_sim_set_probes(sim.ptr, len(face), _ptr(face), _ptr(group), _ptr(weight),
+                                   len(power), _ptr(power), int(capacity), int(every),
+                                   _stream(stream)), "pic_sim_set_probes")
+    sim.probe_groups = len(power)
+    sim.probe_capacity = int(capacity)
+
+
+def pic_probes_read(sim, stream=None):
+    """(records x groups array of the sums recorded since the last read, dropped count)."""
+    out = np.zeros((getattr(sim, "probe_capacity", 0), getattr(sim, "probe_groups", 0)))
+    n, d = _I64(), _I64()
+    _check(_lib.pic_probes_read(sim.ptr, _ptr(out), len(out), ctypes.byref(n),
+                                ctypes.byref(d), _stream(stream)), "pic_probes_read")
+    return out[:n.value].copy(), d.value
 
 
 def pic_sim_set_pusher(sim, pusher):

@@ -2,7 +2,7 @@
 networks (pic_mlp_*) trained on them that answers only where its members agree.
 
 Outputs of one simulated instance (``batch_outputs``), from the azimuthal magnetic field
-sampled every ``every`` steps:
+sampled on the device every ``every`` steps (pic_sim_set_probes):
   * envelope: log10 of the magnetic energy (sum over faces of B_f^2 / 2 times the diagonal
     star_mu^-1 coefficient rho_bar / (mu0 A)) past ``out_z`` in the instance's own frame,
     averaged over 32 equal windows of the run;
@@ -69,13 +69,18 @@ def batch_outputs(instances, dt, bz, steps, every, q, m, w, eps0, mu0, c, sort_i
         d = (z_local[t0:t1] - x["probe"][0]) ** 2 + (cen[t0:t1, 1] - x["probe"][1]) ** 2
         probe[i] = t0 + int(np.argmin(d))
     samples = steps // every
-    energy = np.zeros((n, samples))
-    bprobe = np.zeros((n, samples))
-    for s in range(samples):
-        pic.pic_step(sim, every)
-        B = pic.pic_fields_get(sim)[1]
-        energy[:, s] = np.bincount(inst[out], weights=(coef * B * B)[out], minlength=n)
-        bprobe[:, s] = B[probe]
+    # recorded on the device every `every` steps: group i the magnetic energy past out_z
+    # of instance i, group n + i the probe face's B
+    faces = np.flatnonzero(out)
+    pic.pic_sim_set_probes(sim, np.concatenate([faces, probe]),
+                           np.concatenate([inst[faces], n + np.arange(n)]),
+                           np.concatenate([coef[faces], np.ones(n)]),
+                           np.array([2] * n + [1] * n), capacity=samples, every=every)
+    pic.pic_step(sim, steps)
+    rec, dropped = pic.pic_probes_read(sim)
+    assert len(rec) == samples and dropped == 0
+    energy = rec[:, :n].T
+    bprobe = rec[:, n:].T
     env = np.log10(energy.reshape(n, N_ENV, samples // N_ENV).mean(2) + 1e-300)
     spec = np.abs(np.fft.rfft(bprobe - bprobe.mean(1, keepdims=True), axis=1))
     k = 1 + np.argmax(spec[:, 1:], axis=1)
