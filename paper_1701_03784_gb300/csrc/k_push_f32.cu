@@ -261,11 +261,11 @@ __device__ __forceinline__ void issue_tile(const PushArgs<PF32> &a, PushSmem &sm
 template <bool VAY>
 __device__ __forceinline__ void push_particle(const PushArgs<PF32> &a, int i, int t0, int s0,
                                               int s1, float ur, float up, float uz,
-                                              long long &a1, int &dq0, int &dq1, int &flags,
+                                              long long &a1, int &dq0, int &dq1, int4 &EG,
                                               bool &crossed, QEntry &e) {
     const float4 *R = rec4(a.rec, t0);
     const float4 G = __ldg(R + 0), RH = __ldg(R + 1), CA = __ldg(R + 2), CB = __ldg(R + 3);
-    flags = __ldg(&reinterpret_cast<const int *>(a.rec + t0)[4 * 4 + 3]);
+    EG = __ldg(rec4i(a.rec, t0) + 5);   // edges and orientation flags
     const int s2 = LAM_ONE - s0 - s1;
     const float f0 = fix2f(s0), f1 = fix2f(s1), f2 = fix2f(s2);
 
@@ -523,12 +523,13 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
                 const long long i = base + k;
                 const int t0 = i < n ? b.tri[k] : -1;
                 long long a1 = 0;
-                int dq0 = 0, dq1 = 0, flags = 0;
+                int dq0 = 0, dq1 = 0;
+                int4 EG = make_int4(0, 0, 0, 0);
                 bool crossed = false;
                 QEntry e;
                 if (t0 >= 0)
                     push_particle<VAY>(a, (int)i, t0, b.l0[k], b.l1[k], b.ur[k], b.up[k], b.uz[k],
-                                       a1, dq0, dq1, flags, crossed, e);
+                                       a1, dq0, dq1, EG, crossed, e);
                 // currents of the particles that stay: summed over the lanes of each start
                 // triangle (one 64-bit and two 32-bit sums determine all three edges), one
                 // set of atomics per triangle
@@ -541,8 +542,7 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
                     if (lane == __ffs(grp) - 1) {
                         long long S0, S2;
                         ccw_from(S1, D0, D1, S0, S2);
-                        oriented(flags, S0, S1, S2);
-                        const int4 EG = __ldg(rec4i(a.rec, t0) + 5);
+                        oriented(EG.w, S0, S1, S2);
                         red_add(a.J + EG.x, S0);
                         red_add(a.J + EG.y, S1);
                         red_add(a.J + EG.z, S2);
