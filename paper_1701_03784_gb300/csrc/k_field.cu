@@ -14,7 +14,7 @@ namespace pic {
 // B^{n+1/2} = a_f B^{n-1/2} - b_f dt (D_curl E^n)_f.
 // The same launch clears the step's accumulators (J per edge, Q_abs per node, and in the
 // FP64 build Q^{n+1}, which the particle kernel accumulates).
-template <class P>
+template <class P, bool STATIC, bool LOSS>
 __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
     using R = typename P::R;
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -37,13 +37,13 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
         float E3[3], S3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 3; k++) E3[k] = a.E[ek[k]];
-        if (a.Es) {
+        if constexpr (STATIC) {
 #pragma unroll
             for (int k = 0; k < 3; k++) S3[k] = a.Es[ek[k]];
         }
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const float Ek = a.Es ? E3[k] + S3[k] : E3[k];   // the gather sees the static field
+            const float Ek = STATIC ? E3[k] + S3[k] : E3[k];   // the gather sees the static field
             const int i = (k + 1) % 3, j = (k + 2) % 3;
             const bool fwd = (EG.w >> k) & 1;
             const int ta = fwd ? i : j, hb = fwd ? j : i;
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
         }
         const float Bold = a.B[f];
         float Bnew = Bold - a.dt * curl;
-        if (a.loss_f) {
+        if constexpr (LOSS) {
             const float2 lf = reinterpret_cast<const float2 *>(a.loss_f)[f];
             Bnew = lf.x * Bold - lf.y * (a.dt * curl);
         }
@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const R Ed = a.E[rc.edge[k]];
-        const R Ek = a.Es ? Ed + a.Es[rc.edge[k]] : Ed;   // the gather sees the static field
+        R Ek = Ed;
+        if constexpr (STATIC) Ek += a.Es[rc.edge[k]];   // the gather sees the static field
         int i = (k + 1) % 3, j = (k + 2) % 3;
         bool fwd = (flags >> k) & 1;   // edge runs (k+1) -> (k+2): D_curl entry +1
         int ta = fwd ? i : j, hb = fwd ? j : i;
@@ -83,8 +84,8 @@ __global__ void __launch_bounds__(512) k_field_b(FieldArgs<P> a) {
         curl += fwd ? Ed : -Ed;
     }
     R Bold = a.B[f];
-    R Bnew = a.loss_f ? a.loss_f[2 * f] * Bold - a.loss_f[2 * f + 1] * (a.dt * curl)
-                      : Bold - a.dt * curl;
+    R Bnew = Bold - a.dt * curl;
+    if constexpr (LOSS) Bnew = a.loss_f[2 * f] * Bold - a.loss_f[2 * f + 1] * (a.dt * curl);
     a.B[f] = Bnew;
     rc.bphi = R(0.5) * (Bnew + Bold) * rc.inv_area;
 #pragma unroll
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(512) k_field_r(FieldArgs<P> a) {
 // K4b, sliced ELL SpMV over free edges: E_e += dt (M r)_i (in a lossy layer
 // E_e <- a_e E_e + b_e dt (M r)_i, a = (1 - s)/(1 + s), b = 1/(1 + s), s = sigma dt/(2 eps0)).  A warp owns a slice of 32 rows
 // stored column-major, so each step of the row loop reads 32 consecutive values.
-template <class P>
+template <class P, bool LOSS>
 __global__ void __launch_bounds__(512) k_field_spmv(FieldArgs<P> a) {
     using R = typename P::R;
     int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(512) k_field_spmv(FieldArgs<P> a) {
     }
     if (row < a.nf) {
         const int32_t e = a.free_edges[row];
-        if (a.loss_e) a.E[e] = a.loss_e[2 * row] * a.E[e] + a.loss_e[2 * row + 1] * (a.dt * acc);
+        if constexpr (LOSS) a.E[e] = a.loss_e[2 * row] * a.E[e] + a.loss_e[2 * row + 1] * (a.dt * acc);
         else a.E[e] += a.dt * acc;
     }
 }
@@ -170,7 +171,13 @@ template <class P>
 void launch_field_b(const FieldArgs<P> &a, cudaStream_t s) {
     const int64_t n = std::max(a.N2, std::max(a.N1, a.N0));
     const int b = a.block;
-    k_field_b<P><<<(unsigned)((n + b - 1) / b), b, 0, s>>>(a);
+    const unsigned g = (unsigned)((n + b - 1) / b);
+    // the optional static field and lossy layer as instantiations: none costs the common
+    // case anything
+    if (a.Es && a.loss_f) k_field_b<P, true, true><<<g, b, 0, s>>>(a);
+    else if (a.Es) k_field_b<P, true, false><<<g, b, 0, s>>>(a);
+    else if (a.loss_f) k_field_b<P, false, true><<<g, b, 0, s>>>(a);
+    else k_field_b<P, false, false><<<g, b, 0, s>>>(a);
 }
 
 template <class P>
@@ -179,7 +186,8 @@ void launch_field_e(const FieldArgs<P> &a, cudaStream_t s) {
     const int b = a.block;
     k_field_r<P><<<(unsigned)((n + b - 1) / b), b, 0, s>>>(a);
     int64_t rows = ((a.nf + 31) / 32) * 32;
-    k_field_spmv<P><<<(unsigned)((rows + b - 1) / b), b, 0, s>>>(a);
+    if (a.loss_e) k_field_spmv<P, true><<<(unsigned)((rows + b - 1) / b), b, 0, s>>>(a);
+    else k_field_spmv<P, false><<<(unsigned)((rows + b - 1) / b), b, 0, s>>>(a);
 }
 
 template void launch_field_b<PF32>(const FieldArgs<PF32> &, cudaStream_t);
