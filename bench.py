@@ -436,11 +436,29 @@ def run_mlp_queries(args):
         ms["tensor_cores" if tc else "cuda_cores"] = e0.elapsed_time(e1) / 10
     peak, kind = measured_peak("bf16_tflops")
     tf = flop / (ms["tensor_cores"] * 1e-3) / 1e12
+    # training: Adam steps on minibatches of 128 with the products on either path
+    Xt = torch.tensor(np.random.default_rng(6).uniform(-1, 1, (4096, 6)), dtype=torch.float32,
+                      device="cuda")
+    Tt = torch.tensor(np.random.default_rng(7).normal(0, 1, (4096, S.SIZES[-1])),
+                      dtype=torch.float32, device="cuda")
+    train_ms = {}
+    for batch in (128, 256):
+        for tc in (False, True):
+            pic.pic_mlp_set_training(ens.net, tc)
+            pic.pic_mlp_train(ens.net, Xt, Tt, batch=batch, steps=20, lr=1e-4, seed=1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pic.pic_mlp_train(ens.net, Xt, Tt, batch=batch, steps=500, lr=1e-4, seed=2)
+            torch.cuda.synchronize()
+            key = "batch%d_%s" % (batch, "tensor_cores" if tc else "cuda_cores")
+            train_ms[key] = (time.perf_counter() - t0) / 500 * 1e3
+    pic.pic_mlp_set_training(ens.net, False)
     print(json.dumps({"metric": "surrogate queries/s (5-member ensemble)",
                       "value": n / (ms["tensor_cores"] * 1e-3), "unit": "queries/s",
                       "ms": ms, "roofline": {"bound": "tensor", "achieved": tf, "peak": peak,
                                              "unit": "TFLOP/s", "frac": tf / peak,
-                                             "peak_kind": kind, "flop_per_launch": flop}}))
+                                             "peak_kind": kind, "flop_per_launch": flop},
+                      "train_ms_per_step": train_ms}))
     return 0
 
 

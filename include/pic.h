@@ -406,6 +406,12 @@ pic_status pic_mlp_grad(pic_mlp *m, const float *X, const float *T, int64_t n, d
  * otherwise; synchronous, PIC_ERR_TIMEOUT if a bounded wait gave up). */
 pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int64_t n, int32_t tensor_cores,
                            void *cuda_stream);
+/* Products of pic_mlp_train and pic_mlp_grad (the forward product and both backward
+ * products of every layer) on the tensor cores (tensor_cores != 0: operands rounded to
+ * BF16, FP32 accumulation in TMEM) or on CUDA cores in FP32 (0, the default).  Products
+ * wider than 256 in N or K stay on CUDA cores.  A bounded tensor-core wait that gives up
+ * makes the call that ran it return PIC_ERR_TIMEOUT.  Errors: ARG (a width above 256). */
+pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores);
 void pic_mlp_destroy(pic_mlp *m);
 
 void pic_sim_destroy(pic_sim *s);

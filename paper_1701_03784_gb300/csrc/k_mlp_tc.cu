@@ -250,6 +250,114 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
                      "r"(TMEM_COLS) : "memory");
 }
 
+// ---- products of the training path ----
+// Operand packing (many blocks per product): element (r, c) of the logical R x Cc matrix at
+// src[r sR + c sC] (member stride sz) -> BF16 at core_off(r, c, Cp) of an Rp x Cp tile,
+// zero-padded.  The index along which the source is contiguous runs fastest.
+__global__ void k_tc_pack_op(const float *src, long long sz, int sR, int sC, int R, int Cc,
+                             int Rp, int Cp, uint16_t *dst, long long dz) {
+    const int z = blockIdx.y;
+    const float *a = src + (long long)z * sz;
+    uint16_t *d = dst + (long long)z * dz;
+    const bool rows_fast = sR == 1 && sC != 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Rp * Cp; i += gridDim.x * blockDim.x) {
+        const int r = rows_fast ? i % Rp : i / Cp, c = rows_fast ? i / Rp : i % Cp;
+        d[core_off(r, c, Cp)] =
+            bf16_bits(r < R && c < Cc ? a[(long long)r * sR + (long long)c * sC] : 0.f);
+    }
+}
+
+struct GemmSmem {
+    uint16_t a[TM * KMAX];     // 128 rows of A, core-matrix layout
+    uint16_t b[NMAX * KMAX];   // all of B
+    unsigned long long mbar;   // products done
+    unsigned long long lbar;   // operands landed
+    unsigned int tmem;
+};
+
+struct TcGemmDev {
+    const uint16_t *A, *B;     // packed operands
+    long long sA, sB;          // their member strides (elements)
+    float *C;
+    long long sC;
+    int ldc, M, N, Kp, Np, accumulate;
+    unsigned int *err;
+};
+
+// One CTA: rows [128 x, 128 x + 128) of member y.  One thread brings both packed operands
+// in with bulk copies and issues the products into TMEM; the four warps read their lane
+// quadrants and write (or add to) C.
+__global__ void __launch_bounds__(TM, 1) k_tc_gemm(TcGemmDev g) {
+    extern __shared__ unsigned char raw[];
+    const unsigned pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
+    GemmSmem &sm = *reinterpret_cast<GemmSmem *>(raw + pad);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int z = blockIdx.y, m0 = blockIdx.x * TM;
+    if (tid == 0) {
+        mbar_init(&sm.mbar, 1);
+        mbar_init(&sm.lbar, 1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&sm.tmem)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = sm.tmem;
+    if (tid == 0) {
+        const unsigned ab = (unsigned)(TM * g.Kp * 2), bb = (unsigned)(g.Np * g.Kp * 2);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(smem_u32(&sm.lbar)), "r"(ab + bb) : "memory");
+        bulk_load(sm.a, g.A + (long long)z * g.sA + (long long)m0 * g.Kp, ab, &sm.lbar);
+        bulk_load(sm.b, g.B + (long long)z * g.sB, bb, &sm.lbar);
+    }
+    bool ok = __syncthreads_and(mbar_wait(&sm.lbar, 0u));
+    if (ok) {
+        if (tid == 0) {
+            fence_after();
+            const unsigned a0 = smem_u32(sm.a), b0 = smem_u32(sm.b);
+            const unsigned sbo = (unsigned)g.Kp / 8u * 128u;
+            const unsigned id = idesc_bf16(g.Np);
+            for (int kk = 0; kk < g.Kp / 16; kk++)
+                mma_bf16(tmem, sdesc(a0 + kk * 256u, 128u, sbo), sdesc(b0 + kk * 256u, 128u, sbo),
+                         id, kk > 0);
+            mma_commit(&sm.mbar);
+        }
+        ok = __syncthreads_and(mbar_wait(&sm.mbar, 0u));
+    }
+    if (ok) {
+        fence_after();
+        const int m = m0 + warp * 32 + lane;
+        float *c = g.C + (long long)z * g.sC + (long long)m * g.ldc;
+        for (int c0 = 0; c0 < g.Np; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+            if (m < g.M) {
+#pragma unroll
+                for (int j = 0; j < 16; j++)
+                    if (c0 + j < g.N) c[c0 + j] = g.accumulate ? c[c0 + j] + v[j] : v[j];
+            }
+        }
+    } else {
+        // a wait gave up: count it, give the copies and products in flight one more bounded
+        // wait, free TMEM below
+        if (tid == 0) {
+            atomicAdd(g.err, 1u);
+            mbar_wait(&sm.lbar, 0u);
+            mbar_wait(&sm.mbar, 0u);
+        }
+        __syncthreads();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS) : "memory");
+}
+
 // FP32 parameters -> BF16 core-matrix weights and FP32 biases, zero-padded
 struct PackArgs {
     long long woff[MLP_MAX_LAYERS], boff[MLP_MAX_LAYERS];
@@ -277,6 +385,31 @@ void mlp_tc_pack(const MlpTc &tc, const float *params, long long P, const long l
         pa.boff[l] = boff[l];
     }
     k_mlp_pack<<<dim3(64, tc.E * tc.L), 256, 0, s>>>(tc, params, P, pa);
+}
+
+bool mlp_tc_gemm(const TcGemmOp &g, int E, uint16_t *scratch_a, uint16_t *scratch_b,
+                 unsigned int *err, cudaStream_t s) {
+    if (g.N < 1 || g.N > NMAX || g.K < 1 || g.K > KMAX || g.M < 1) return false;
+    static bool attr[64] = {};   // the shared-memory opt-in, once per device
+    const int smem = (int)sizeof(GemmSmem) + 1024;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr[dev & 63]) {
+        if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess)
+            return false;
+        attr[dev & 63] = true;
+    }
+    const int Mp = (g.M + TM - 1) / TM * TM, Kp = (g.K + 15) / 16 * 16, Np = (g.N + 15) / 16 * 16;
+    // A as an M x K matrix; B as the N x K matrix of its transpose (both K-major)
+    k_tc_pack_op<<<dim3(64, E), 256, 0, s>>>(g.A, g.sAz, g.sAm, g.sAk, g.M, g.K, Mp, Kp,
+                                             scratch_a, (long long)Mp * Kp);
+    k_tc_pack_op<<<dim3(64, E), 256, 0, s>>>(g.B, g.sBz, g.sBn, g.sBk, g.N, g.K, Np, Kp,
+                                             scratch_b, (long long)Np * Kp);
+    const TcGemmDev d{scratch_a, scratch_b, (long long)Mp * Kp, (long long)Np * Kp, g.C, g.sCz,
+                      g.ldc, g.M, g.N, Kp, Np, g.accumulate, err};
+    k_tc_gemm<<<dim3((unsigned)(Mp / TM), (unsigned)E), TM, smem, s>>>(d);
+    return true;
 }
 
 pic_status mlp_tc_forward(const MlpTc &tc, const float *X, float *Y, int64_t n, cudaStream_t s) {

@@ -1,7 +1,8 @@
 // Surrogate network ensemble: small multilayer perceptrons (tanh-GELU hidden layers, linear
 // output) that map sweep parameters to simulation outputs, trained and evaluated on the
 // GPU by the kernels in this file (FP32 on CUDA cores) and k_mlp_tc.cu (BF16 tensor-core
-// inference).  The paper has no counterpart.
+// inference, and optionally the training products: pic_mlp_set_training).  The paper has
+// no counterpart.
 //
 // Layout: per member, the layers' parameters one after another, W_l (n_out x n_in,
 // row-major) then b_l; members follow each other at a fixed stride.  Activations are
@@ -176,6 +177,11 @@ struct MlpImpl {
     long long adam_step = 0;
     MlpTc tc;               // BF16 tensor-core copy of the parameters
     bool tc_dirty = true;   // parameters changed since it was packed
+    // training products on the tensor cores (pic_mlp_set_training): packed BF16 operand
+    // scratch and the bounded-wait counter
+    bool train_tc = false, gemm_tc = false;
+    uint16_t *tsa = nullptr, *tsb = nullptr;
+    unsigned int *terr = nullptr;
 
     ~MlpImpl() {
         cudaSetDevice(device);
@@ -243,6 +249,11 @@ struct MlpImpl {
             if ((st = dalloc(tc.w, E * tc.wmember)) || (st = dalloc(tc.b, E * tc.bmember)) ||
                 (st = dalloc(tc.err, 1)))
                 return st;
+            const long long mp = (std::max(max_batch, maxw) + 127) / 128 * 128;
+            if ((st = dalloc(tsa, (long long)E * mp * 256)) ||
+                (st = dalloc(tsb, (long long)E * 256 * 256)) || (st = dalloc(terr, 1)))
+                return st;
+            PIC_CUDA_TRY(cudaMemset(terr, 0, sizeof(unsigned int)));
         }
         PIC_CUDA_TRY(cudaMemset(params, 0, sizeof(float) * E * P));
         PIC_CUDA_TRY(cudaMemset(am, 0, sizeof(float) * E * P));
@@ -250,7 +261,27 @@ struct MlpImpl {
         return PIC_OK;
     }
 
+    // timeouts of the training products since the last check (synchronises when the
+    // tensor-core products were on)
+    pic_status tc_errors(const char *who, cudaStream_t s) {
+        if (!train_tc || !terr) return PIC_OK;
+        unsigned int e = 0;
+        PIC_CUDA_TRY(cudaMemcpyAsync(&e, terr, sizeof e, cudaMemcpyDeviceToHost, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (e) {
+            PIC_CUDA_TRY(cudaMemsetAsync(terr, 0, sizeof e, s));
+            set_error("%s: %u tensor-core waits timed out", who, e);
+            return PIC_ERR_TIMEOUT;
+        }
+        return PIC_OK;
+    }
+
     void gemm(const GemmArgs &g, cudaStream_t s) {
+        if (gemm_tc) {
+            const TcGemmOp op{g.A, g.B, g.C, g.M, g.N, g.K, g.sAz, g.sBz, g.sCz,
+                              g.sAm, g.sAk, g.sBk, g.sBn, g.ldc, g.accumulate};
+            if (mlp_tc_gemm(op, E, tsa, tsb, terr, s)) return;
+        }
         dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, E);
         k_gemm<<<grid, dim3(GT, GT), 0, s>>>(g);
     }
@@ -401,8 +432,12 @@ extern "C" pic_status pic_mlp_grad(pic_mlp *m, const float *X, const float *T, i
     k_gather<<<dim3(blocks(rows), x.E), 256, 0, s>>>(X, T, x.act[0], x.Tb, n, rows, x.max_batch,
                                                      x.sz[0], x.sz[x.L], 0, 0, 0);
     PIC_CUDA_TRY(cudaMemsetAsync(x.loss, 0, sizeof(float) * x.E, s));
+    x.gemm_tc = x.train_tc;
     x.forward(rows, x.act[0], (long long)x.max_batch * x.sz[0], s);
     x.backward(rows, x.loss, s);
+    x.gemm_tc = false;
+    pic_status ts = x.tc_errors("pic_mlp_grad", s);
+    if (ts != PIC_OK) return ts;
     std::vector<float> h(x.E * x.P), hl(x.E);
     PIC_CUDA_TRY(cudaMemcpyAsync(h.data(), x.grads, sizeof(float) * h.size(),
                                  cudaMemcpyDeviceToHost, s));
@@ -426,6 +461,7 @@ extern "C" pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *T, 
     cudaStream_t s = (cudaStream_t)st;
     const long long np = x.E * x.P;
     x.tc_dirty = true;
+    x.gemm_tc = x.train_tc;
     for (long long k = 0; k < steps; k++) {
         k_gather<<<dim3(blocks(batch), x.E), 256, 0, s>>>(X, T, x.act[0], x.Tb, n, batch,
                                                           x.max_batch, x.sz[0], x.sz[x.L], seed,
@@ -441,7 +477,10 @@ extern "C" pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *T, 
         k_adam<<<blocks(np), 256, 0, s>>>(x.params, x.grads, x.am, x.av, np, (float)lr, b1, b2,
                                           1e-8f, c1, c2);
     }
+    x.gemm_tc = false;
     PIC_CUDA_TRY(cudaGetLastError());
+    pic_status ts = x.tc_errors("pic_mlp_train", s);
+    if (ts != PIC_OK) return ts;
     if (last_loss) {
         std::vector<float> hl(x.E, 0.f);
         if (steps > 0)
@@ -481,6 +520,17 @@ extern "C" pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int6
             x.act[x.L], Y, rows, dout, x.max_batch, n, c0);
     }
     PIC_CUDA_TRY(cudaGetLastError());
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores) {
+    MLP_CHECK(m, "pic_mlp_set_training");
+    MlpImpl &x = *m->impl;
+    if (tensor_cores && !x.tc.ok) {
+        set_error("pic_mlp_set_training: tensor-core products need widths of at most 256");
+        return PIC_ERR_ARG;
+    }
+    x.train_tc = tensor_cores != 0;
     return PIC_OK;
 }
 

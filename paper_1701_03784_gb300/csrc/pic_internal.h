@@ -48,6 +48,22 @@ void mlp_tc_pack(const MlpTc &tc, const float *params, long long P, const long l
                  const long long *boff, cudaStream_t s);
 // Y (E x n x outputs, FP32) from X (n x inputs, FP32); PIC_ERR_TIMEOUT if a wait gave up
 pic_status mlp_tc_forward(const MlpTc &tc, const float *X, float *Y, int64_t n, cudaStream_t s);
+// One product of the training path on the tensor cores, per member z of E:
+// C(z)[m][n] (+)= sum_k A(z, m, k) B(z, k, n), operands FP32 addressed by strides (as the
+// CUDA-core GEMM takes them), rounded to BF16 into the packed scratch buffers (A: E x
+// roundup(M, 128) x roundup(K, 16), B: E x roundup(N, 16) x roundup(K, 16) elements), FP32
+// accumulation in TMEM.  Needs N <= 256 and K <= 256 (false: not done).  Bounded waits
+// that give up are counted in *err.
+struct TcGemmOp {
+    const float *A, *B;
+    float *C;
+    int M, N, K;
+    long long sAz, sBz, sCz;
+    int sAm, sAk, sBk, sBn, ldc;
+    int accumulate;
+};
+bool mlp_tc_gemm(const TcGemmOp &g, int E, uint16_t *scratch_a, uint16_t *scratch_b,
+                 unsigned int *err, cudaStream_t s);
 #define PIC_CUDA_TRY(expr)                                                              \
     do {                                                                                \
         cudaError_t err__ = (expr);                                                     \

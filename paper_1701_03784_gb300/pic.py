@@ -88,6 +88,7 @@ _SIGS = {
     "pic_mlp_train": [_P, _P, _P, _I64, _I32, _I64, _D, ctypes.c_uint64, _P, _P],
     "pic_mlp_grad": [_P, _P, _P, _I64, _P, _P, _P],
     "pic_mlp_forward": [_P, _P, _P, _I64, _I32, _P],
+    "pic_mlp_set_training": [_P, _I32],
     "pic_fields_set": [_P, _P, _P, _P],
     "pic_particles_inject": [_P, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _P],
     "pic_step": [_P, _I64, _P],
@@ -579,6 +580,11 @@ def pic_mlp_grad(m, X, T, stream=None):
     _check(_lib.pic_mlp_grad(m.ptr, _dev(X, "X"), _dev(T, "T"), X.shape[0], _ptr(g), _ptr(loss),
                              _stream(stream)), "pic_mlp_grad")
     return g, loss
+
+
+def pic_mlp_set_training(m, tensor_cores):
+    """Training and gradient products on the tensor cores (BF16 operands) or not."""
+    _check(_lib.pic_mlp_set_training(m.ptr, 1 if tensor_cores else 0), "pic_mlp_set_training")
 
 
 def pic_mlp_forward(m, X, tensor_cores=False, out=None, stream=None):
