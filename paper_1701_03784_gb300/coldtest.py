@@ -3,9 +3,9 @@ cell between two ripple maxima with conducting end planes has, among its TM01-li
 resonances, the 0 point (the pattern uniform in z) and the pi point (one half-wave along
 z) of the periodic structure's dispersion.  The field solver rings the cell down from the
 line integrals of a cylinder's TM010 + TM011 patterns and the two mode projections'
-frequencies are fitted (a sinusoid plus offset by least squares, started from the
-windowed spectrum's peak).  Conformal and staircased meshes of the same spacing give the
-staircasing error."""
+frequencies are fitted (two sinusoids plus offset by least squares, started from the
+windowed spectrum's two largest peaks).  Conformal and staircased meshes of the same
+spacing give the staircasing error."""
 import numpy as np
 
 from . import pic
@@ -15,15 +15,27 @@ from workloads.meshes import sws_cell_mesh
 
 
 def _frequency(t, a):
+    """Frequency (Hz) of the strongest tone of a(t): two sinusoids and an offset fitted by
+    least squares, started from the two largest peaks of the windowed spectrum (the other
+    mode leaks into every projection)."""
     from scipy.optimize import least_squares
     n = len(a)
     spec = np.abs(np.fft.rfft((a - a.mean()) * np.hanning(n), 16 * n))
-    f0 = np.fft.rfftfreq(16 * n, t[1] - t[0])[1 + np.argmax(spec[1:])]
+    freqs = np.fft.rfftfreq(16 * n, t[1] - t[0])
+    k1 = 1 + int(np.argmax(spec[1:]))
+    # the second peak: the largest at least two resolution widths away from the first
+    far = np.abs(np.arange(len(spec)) - k1) > 2 * 16
+    far[0] = False
+    k2 = int(np.argmax(np.where(far, spec, 0.0)))
+    w1, w2 = 2.0 * np.pi * freqs[k1], 2.0 * np.pi * freqs[k2]
 
     def res(p):
-        return p[0] * np.cos(p[2] * t) + p[1] * np.sin(p[2] * t) + p[3] - a
-    p = least_squares(res, [a.std(), 0.0, 2.0 * np.pi * f0, a.mean()], x_scale="jac").x
-    return p[2] / (2.0 * np.pi)
+        return (p[0] * np.cos(p[2] * t) + p[1] * np.sin(p[2] * t) + p[3] * np.cos(p[5] * t)
+                + p[4] * np.sin(p[5] * t) + p[6] - a)
+    p = least_squares(res, [a.std(), 0.0, w1, 0.1 * a.std(), 0.0, w2, a.mean()],
+                      x_scale="jac").x
+    main = p[2] if np.hypot(p[0], p[1]) >= np.hypot(p[3], p[4]) else p[5]
+    return main / (2.0 * np.pi)
 
 
 def ring_down(n_tri, staircase, duration=1.5e-9, precision=pic.PIC_FP64, r0=15.0e-3,
