@@ -155,10 +155,27 @@ __global__ void __launch_bounds__(512) k_field_spmv(FieldArgs<P> a) {
     int64_t off = a.ell_off[slice];
     int width = (int)((a.ell_off[slice + 1] - off) >> 5);
     R acc = 0;
-    for (int k = 0; k < width; k++) {
-        int64_t idx = off + ((int64_t)k << 5) + lane;
-        int32_t col = a.ell_col[idx];
-        acc += a.ell_val[idx] * a.r[col];
+    int k = 0;
+    // four columns' indices and values in flight before their gathers (the sum keeps the
+    // column order)
+    for (; k + 4 <= width; k += 4) {
+        int32_t col[4];
+        R val[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t idx = off + ((int64_t)(k + u) << 5) + lane;
+            col[u] = a.ell_col[idx];
+            val[u] = a.ell_val[idx];
+        }
+        R rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) rv[u] = a.r[col[u]];
+#pragma unroll
+        for (int u = 0; u < 4; u++) acc += val[u] * rv[u];
+    }
+    for (; k < width; k++) {
+        const int64_t idx = off + ((int64_t)k << 5) + lane;
+        acc += a.ell_val[idx] * a.r[a.ell_col[idx]];
     }
     if (row < a.nf) {
         const int32_t e = a.free_edges[row];
