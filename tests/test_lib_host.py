@@ -97,3 +97,16 @@ def test_host_setup_matches_oracle(pic, which):
     assert np.allclose(vv, M.data, rtol=1e-9, atol=1e-12 * np.abs(M.data).max())
     dt_o, _ = dt_stable(om, M, hodge_mu_inv(om, mu0))
     assert abs(dt - dt_o) <= 1e-9 * dt_o
+
+
+def test_header_is_plain_c():
+    """include/pic.h compiles as C99 (the boundary takes plain pointers and sizes only)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    hdr = os.path.join(os.path.dirname(__file__), "..", "include", "pic.h")
+    r = subprocess.run([gcc, "-std=c99", "-fsyntax-only", "-Wall", "-Werror", "-x", "c", hdr],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
