@@ -237,10 +237,21 @@ def run_sweep(args):
     import paper_1701_03784_gb300 as pkg
     pkg.build()
     from paper_1701_03784_gb300 import pic
-    from workloads.sweep import sweep_instance, union, WEIGHT
+    from paper_1701_03784_gb300.batch import partition
+    from workloads.sweep import sweep_instance, sweep_params, sweep_particles, union, WEIGHT
     from workloads.bwo import BZ_BWO
+    # across GPUs the instances are sharded (one union per rank, nothing exchanged)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t_setup = time.time()
-    ins = [sweep_instance(i) for i in range(args.sweep)]
+    work = [sweep_particles(i) + sweep_params(i)["n_tri"] for i in range(args.sweep)]
+    mine = partition(work, world)[rank]
+    ins = [sweep_instance(i) for i in mine]
     u = union(ins)
 
     def make(x):
@@ -282,17 +293,26 @@ def run_sweep(args):
         ms_p += ms
         del mesh
     k = args.sweep_steps
+    # the job: the slowest rank's times, every rank's particles
+    (ms_b, ms_p), (n_part, n_tris) = reduce_over_ranks(ms_b, ms_p, len(u["z"]), len(u["tris"]),
+                                                        dist, device="cuda")
     step_b, step_p = ms_b / k, ms_p / k
-    n_part = len(u["z"])
     runs_b = args.sweep * 3600.0 / (SWEEP_RUN_STEPS * step_b * 1e-3)
     runs_p = args.sweep * 3600.0 / (SWEEP_RUN_STEPS * step_p * 1e-3)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     print(json.dumps({
         "metric": "batched runs/h vs plain", "value": runs_b, "unit": "runs/h",
         "higher_is_better": True, "plain": runs_p, "speedup": runs_b / runs_p,
-        "n_gpus": 1, "steps": k, "warmup": args.sweep_warmup, "dtype": "f32", "data": "synthetic",
+        "n_gpus": world, "scaling": "strong", "steps": k, "warmup": args.sweep_warmup,
+        "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched ripple sweep, %d BWO instances (seeds 0..%d)"
                                % (args.sweep, args.sweep - 1),
-                   "instances": args.sweep, "triangles": int(len(u["tris"])),
+                   "instances": args.sweep, "triangles": int(n_tris),
+                   "parallelism": "instances sharded over %d GPUs" % world if world > 1 else "single",
                    "particles": int(n_part), "dt_s": dt, "sort_interval": args.sort_interval,
                    "run_steps": SWEEP_RUN_STEPS, "cuda_graph": not args.no_graph,
                    "tuned_batched": tuned[0]},

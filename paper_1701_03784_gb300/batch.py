@@ -48,3 +48,18 @@ def union(instances, gap=GAP):
                 z=cat(zs), r=cat(rs), ur=cat(urs), up=cat(ups), uz=cat(uzs),
                 node_off=np.array(node_off), tri_off=np.array(tri_off),
                 part_off=np.array(part_off), shift=np.array(shift))
+
+
+def partition(work, n_ranks):
+    """Instances to ranks for a sweep sharded across GPUs (one union per rank, no data
+    exchanged): longest work first, each to the least-loaded rank (ties: the lower rank),
+    so the slowest rank carries at most 4/3 of the optimum.  ``work`` is a per-instance cost
+    (e.g. particles + triangles).  Returns one ascending list of instance indices per rank."""
+    work = np.asarray(work, float)
+    loads = np.zeros(n_ranks)
+    parts = [[] for _ in range(n_ranks)]
+    for i in sorted(range(len(work)), key=lambda k: (-work[k], k)):
+        r = int(np.argmin(loads))
+        parts[r].append(i)
+        loads[r] += work[i]
+    return [sorted(p) for p in parts]

@@ -43,3 +43,23 @@ def test_union_is_the_instances_side_by_side(pic):
     dts = [pic.pic_spai_build(mk(x), 2, 1e-4) for x in ins]
     dtu = pic.pic_spai_build(mu, 2, 1e-4)
     assert abs(dtu - min(dts)) <= 1e-3 * min(dts)
+
+
+def test_partition_of_instances_over_ranks():
+    """Every instance on exactly one rank, ascending lists, and the greedy longest-first
+    bound: no rank above 4/3 of the best possible makespan's lower bound (the larger of
+    the mean load and the largest instance)."""
+    from paper_1701_03784_gb300.batch import partition
+    from workloads.sweep import sweep_params, sweep_particles
+    work = [sweep_particles(i) + sweep_params(i)["n_tri"] for i in range(64)]
+    for n in (1, 2, 3, 8):
+        parts = partition(work, n)
+        assert len(parts) == n
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(64))
+        assert all(p == sorted(p) for p in parts)
+        loads = [sum(work[i] for i in p) for p in parts]
+        bound = max(sum(work) / n, max(work))
+        assert max(loads) <= 4.0 / 3.0 * bound
+    assert partition(work, 2) == partition(work, 2)
+    assert partition([5.0, 1.0, 1.0], 4) == [[0], [1], [2], []]

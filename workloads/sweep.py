@@ -38,6 +38,19 @@ def sweep_params(i):
                 current=rng.uniform(1e3, 5e3), n_tri=int(rng.integers(20_000, 80_001)))
 
 
+def sweep_particles(i, scale=1.0):
+    """Particle count of instance i: its beam charge in the slow-wave section over the
+    common weight, clipped to [N_MIN, N_MAX], times scale."""
+    p = sweep_params(i)
+    zs0, zs1 = bwo_wall(r0=R0, ripple=p["depth"], period=p["period"],
+                        n_periods=p["n_periods"], guide=GUIDE)[2]
+    gamma = 1.0 + p["voltage"] / MC2_VOLTS
+    vz = C0 * math.sqrt(1.0 - 1.0 / gamma ** 2)
+    charge = p["current"] * (zs1 - zs0) / vz
+    n = int(min(max(round(charge / (QE * WEIGHT)), N_MIN), N_MAX))
+    return max(1, int(round(n * scale)))
+
+
 def sweep_instance(i, scale=1.0, mesh_scale=1.0):
     """Mesh and beam of instance i.  ``scale`` multiplies the particle count and
     ``mesh_scale`` the triangle count (tests and surrogate data use fractions of them)."""
@@ -57,9 +70,7 @@ def sweep_instance(i, scale=1.0, mesh_scale=1.0):
                                     n_periods=p["n_periods"], guide=GUIDE)
     gamma = 1.0 + p["voltage"] / MC2_VOLTS
     vz = C0 * math.sqrt(1.0 - 1.0 / gamma ** 2)
-    charge = p["current"] * (zs1 - zs0) / vz
-    n = int(min(max(round(charge / (QE * WEIGHT)), N_MIN), N_MAX))
-    n = max(1, int(round(n * scale)))
+    n = sweep_particles(i, scale)
     rb = 0.7 * (R0 - p["depth"])
     z, r, ur, up, uz = bwo_beam(n, r_in=rb - 0.05e-2, r_out=rb + 0.05e-2, z0=zs0, z1=zs1,
                                 voltage=p["voltage"], seed=4000 + i)
