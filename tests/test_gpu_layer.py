@@ -92,3 +92,32 @@ def test_graded_layer_absorbs_a_guided_pulse_on_the_gpu(pic, guide):
         pic.pic_sim_destroy(sim)
     assert left[False] > 0.95 and left[True] < 0.01
     pic.pic_mesh_destroy(mesh)
+
+
+def test_removing_the_layer_restores_the_lossless_update(pic, guide):
+    """A layer set and then removed before any step leaves the fields bit-identical to a
+    simulation that never had one (FP32), and the probes of a simulation can be removed."""
+    arrays, oracle = guide
+    m = oracle.mesh
+    mesh = pic.pic_mesh_create(*arrays, precision=pic.PIC_FP32)
+    dt = 0.5 * pic.pic_spai_build(mesh)
+    E0 = _pulse(m)
+    out = []
+    for layer in (False, True):
+        sim = pic.pic_sim_create(mesh, dt, 0.0, 16)
+        pic.pic_fields_set(sim, E0, np.zeros(m.N2))
+        if layer:
+            pic.pic_sim_set_loss(sim, *ports.graded_layer(
+                m.nodes, m.edge_nodes, m.tris, 12.0, 16.0, ports.sigma_max_for(1e-4, 4.0, 3)))
+            pic.pic_sim_set_loss(sim, None, None)
+            pic.pic_sim_set_probes(sim, [0, 1], [0, 0], [1.0, 1.0], [2], capacity=8, every=1)
+            pic.pic_sim_set_probes(sim, [], [], [], [], capacity=8, every=1)
+        pic.pic_step(sim, 50)
+        out.append(pic.pic_fields_get(sim))
+        if layer:
+            with pytest.raises(pic.PicError) as e:
+                pic.pic_probes_read(sim)
+            assert e.value.status == pic.PIC_ERR_STATE
+        pic.pic_sim_destroy(sim)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    pic.pic_mesh_destroy(mesh)
