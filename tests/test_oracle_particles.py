@@ -8,6 +8,7 @@ import pytest
 import workloads as W
 from oracle import OracleSim
 from oracle.operators import Mesh
+from oracle import particles as TPart
 
 
 def _grad_by_solve(p):
@@ -259,3 +260,110 @@ def test_absorbed_charge_enters_dce(cavity):
     assert abs(s.Qabs.sum() - s.q_src) < 1e-15
     assert np.abs(s.dce_residual()).max() * dt < 1e-15
     assert np.all(s.Q == 0)
+
+
+def test_rotational_field_fixes_faraday_sign_and_time_centred_B():
+    """E = (a/2)(-rho, z) in (E_z, E_rho) is a rotation field, which Whitney 1-forms
+    reproduce exactly (App. A), with (curl E)_phi = dE_rho/dz - dE_z/drho = a.  Faraday's
+    law then raises B_phi by -a dt per step on every face away from the walls (Eq.
+    full_d_dfl; B_phi = B_f / A, Sec. 3.2).  A particle moving in the meridian plane feels
+    E at its position and the time-centred B_phi = B0 - a dt / 2, and its new momentum
+    must solve Boris's form of Eq. DLE: u1 - u0 = 2h (E + (u0 + u1) / (2 gamma(u0 + h E))
+    x B) with h = q dt / (2 m).  This fixes the orientation of D_curl against +phi, the
+    1/A of the 2-form, the averaging of B and the gathered E together."""
+    nodes, tris, be, bt = W.rect_mesh(1.0, 1.0, 600, 21)
+    s = OracleSim(nodes, tris, be, bt)
+    m = s.mesh
+    dt = 0.5 * s.dt_max
+    s.create(dt)
+    a, B0 = 3.0, 2.0
+
+    def field(z, r):
+        return np.stack([-0.5 * a * r, 0.5 * a * z], -1)          # (E_z, E_rho)
+
+    pt, ph = m.nodes[m.edge_nodes[:, 0]], m.nodes[m.edge_nodes[:, 1]]
+    E = np.einsum("ed,ed->e", field(*(0.5 * (pt + ph)).T), ph - pt)   # exact for linear E
+    s.set_fields(E, B0 * m.area)
+    Bh = s.field_b_half()
+    away = ~np.any(m.edge_tag[m.tri_edges] == 1, axis=1)
+    assert away.sum() > m.N2 // 2
+    assert np.allclose(Bh[away] / m.area[away], B0 - a * dt, rtol=0, atol=1e-12)
+
+    z0, r0 = 0.47, 0.53
+    u0 = np.array([0.3, 0.0, 0.6])                                  # (u_rho, u_phi, u_z)
+    q, mass = -1.0, 1.0
+    s.inject([z0], [r0], [u0[0]], [u0[1]], [u0[2]], q, mass, 1e-9)
+    assert away[s.tri[0]]
+    s.push_particles(Bh)
+    u1 = s.u[0]
+    Ez, Er = field(z0, r0)
+    Ef = np.array([Er, 0.0, Ez])
+    Bf = np.array([0.0, B0 - 0.5 * a * dt, 0.0])
+    h = q * dt / (2 * mass)
+    gm = math.sqrt(1.0 + np.sum((u0 + h * Ef) ** 2))
+    rhs = 2 * h * (Ef + np.cross(0.5 * (u0 + u1) / gm, Bf))
+    assert abs(u1[1]) < 1e-15
+    assert np.abs(u1 - u0 - rhs).max() < 1e-13
+    # the magnetic part is not negligible: B_phi at n+1/2 alone would miss by far more
+    Bn = np.array([0.0, B0 - a * dt, 0.0])
+    assert np.abs(u1 - u0 - 2 * h * (Ef + np.cross(0.5 * (u0 + u1) / gm, Bn))).max() > 1e-6
+
+
+def _path_current(m, r0, r1):
+    """int W1_e . dr along the straight segment r0 -> r1, cell by cell: the cuts where it
+    meets any mesh edge (brute force over all edges), the containing triangle of each
+    piece by point location, and a 2-point Gauss rule on each piece (exact: W1 is linear
+    inside a triangle), with gradients and lambda from linear solves."""
+    a, b = m.nodes[m.edge_nodes[:, 0]], m.nodes[m.edge_nodes[:, 1]]
+    d, e, w = r1 - r0, b - a, a - r0
+    det = e[:, 0] * d[1] - d[0] * e[:, 1]            # of [d, -e] (s, t) = w
+    ok = np.abs(det) > 1e-14
+    sd = np.where(ok, det, 1.0)
+    s = (e[:, 0] * w[:, 1] - w[:, 0] * e[:, 1]) / sd
+    t = (d[0] * w[:, 1] - w[:, 0] * d[1]) / sd
+    cut = ok & (s > 0) & (s < 1) & (t >= 0) & (t <= 1)
+    ss = np.concatenate([[0.0], np.sort(s[cut]), [1.0]])
+    x, wq = np.polynomial.legendre.leggauss(2)
+    x, wq = 0.5 * (x + 1), 0.5 * wq
+    J = np.zeros(m.N1)
+    for s0, s1 in zip(ss[:-1], ss[1:]):
+        if s1 - s0 < 1e-13:
+            continue
+        mid = r0 + 0.5 * (s0 + s1) * d
+        tri, _ = TPart.locate(m, [mid[0]], [mid[1]])
+        T = int(tri[0])
+        p = m.nodes[m.tris[T]]
+        G = _grad_by_solve(p)
+        for xi, wi in zip(x, wq):
+            r = r0 + (s0 + xi * (s1 - s0)) * d
+            lam = _lam_by_solve(p, r[0], r[1])
+            for k in range(3):
+                ta, hb = m.edge_tail_head(T, k)
+                J[m.tri_edges[T, k]] += wi * (s1 - s0) * (lam[ta] * G[hb] - lam[hb] * G[ta]) @ d
+    return J
+
+
+def test_multi_cell_current_is_the_line_integral_over_the_crossed_cells(cavity):
+    """Eq. current summed over the pieces of a path that crosses several cells: for
+    force-free particles on straight meridian paths (u_phi = 0), J must equal (q/dt) times
+    the line integral of the piecewise Whitney 1-forms, computed here cell by cell from
+    the path's exact cuts with the mesh edges."""
+    s = _fresh(cavity)
+    m = s.mesh
+    s.create(0.5 * s.dt_max)
+    dt = s.dt = 0.5                      # particle-only step; the fields stay zero
+    rng = np.random.default_rng(21)
+    n = 30
+    r0 = np.stack([rng.uniform(0.1, 0.9, n), rng.uniform(0.08, 0.42, n)], 1)
+    ang = rng.uniform(0, 2 * np.pi, n)
+    r1 = r0 + rng.uniform(0.05, 0.15, n)[:, None] * np.stack([np.cos(ang), np.sin(ang)], 1)
+    r1 = np.clip(r1, [0.02, 0.02], [0.98, 0.48])
+    v = (r1 - r0) / dt                   # (v_z, v_rho), |v| < c = 1
+    gam = 1.0 / np.sqrt(1.0 - np.sum(v * v, 1))
+    s.inject(r0[:, 0], r0[:, 1], gam * v[:, 1], np.zeros(n), gam * v[:, 0], -1.0, 1.0, 1e-3)
+    s.push_particles(s.field_b_half())
+    assert np.all(s.tri >= 0) and s.counters[2] > 3 * n
+    zn, rn = s.positions()
+    assert np.allclose(zn, r1[:, 0], atol=1e-12) and np.allclose(rn, r1[:, 1], atol=1e-12)
+    ref = sum(_path_current(m, r0[i], r1[i]) for i in range(n)) * (s.q_src / dt)
+    assert np.abs(s.J - ref).max() <= 1e-12 * np.abs(ref).max()

@@ -86,3 +86,33 @@ def test_vay_leaves_a_force_free_particle_unaccelerated(gam):
     if gam < 2:
         ub = P.kick(P.BORIS, u0, E, B, 0.05, C)
         assert np.abs(ub - u0).max() > 1e-6 * umag
+
+
+def test_cycle_uses_the_selected_pusher():
+    """Through a whole particle step of the cycle: a particle moving in phi at the E x B
+    drift speed (uniform E_rho = -v_phi B_z, guide field B_z) is force-free, so with the
+    Vay update its momentum only turns with the rotation back to the meridian plane, by
+    theta = atan2(v_phi dt, rho) (Eq. DNE); Boris leaves a visible error at gamma = 1.01."""
+    import workloads as W
+    from oracle import OracleSim
+
+    nodes, tris, be, bt = W.rect_mesh(1.0, 1.0, 400, 21)
+    out = {}
+    for pusher in (P.BORIS, P.VAY):
+        s = OracleSim(nodes, tris, be, bt)
+        m = s.mesh
+        dt, bz, gam = 0.5 * s.dt_max, 10.0, 1.01
+        s.create(dt, bz=bz)
+        s.pusher = pusher
+        uphi = math.sqrt(gam ** 2 - 1.0)
+        E_rho = -(uphi / gam) * bz
+        d = m.nodes[m.edge_nodes[:, 1]] - m.nodes[m.edge_nodes[:, 0]]
+        s.set_fields(E_rho * d[:, 1], np.zeros(m.N2))        # line integrals of E_rho
+        rho0 = 0.5
+        s.inject([0.5], [rho0], [0.0], [uphi], [0.0], 1.0, 1.0, 1e-9)
+        s.push_particles(s.field_b_half())
+        out[pusher] = s.u[0].copy()
+    th = math.atan2(uphi / gam * dt, rho0)
+    expect = np.array([math.sin(th) * uphi, math.cos(th) * uphi, 0.0])
+    assert np.abs(out[P.VAY] - expect).max() <= 1e-14 * uphi
+    assert np.abs(out[P.BORIS] - expect).max() > 1e-9 * uphi

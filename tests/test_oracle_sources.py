@@ -153,3 +153,27 @@ def test_gauss_law_of_a_charged_shell_fixes_the_ring_normalisation():
                        & (m.nodes[:, 0] > 1.0) & (m.nodes[:, 0] < 3.0))
     expect = n * w * q / (2 * math.pi * 1.0 * 4.0) * np.log(1.0 / m.nodes[k, 1])
     assert np.abs(phi[k] - expect).max() < 0.005 * np.abs(expect).max()
+
+
+def test_static_field_drives_particles_but_not_the_leapfrog():
+    """The gun field of a planar gap (phi = V z / L, edge values -V dz / L) is added to E
+    at the gather only: particles at rest gain u_z = (q/m)(-V/L) dt in one step, while
+    the dynamic fields, with no current (weight 0), stay exactly zero."""
+    nodes, tris, be, bt = W.cavity_mesh(a=0.5, L=1.0, n_tri=800, seed=5)
+    s = OracleSim(nodes, tris, be, bt)
+    m = s.mesh
+    dt = 0.5 * s.dt_max
+    s.create(dt)
+    V = 2.0
+    held = np.flatnonzero((m.nodes[:, 0] == 0.0) | (m.nodes[:, 0] == 1.0))
+    _, Es = S.static_potential(m, s.star_eps, held, V * m.nodes[held, 0])
+    s.set_static_field(Es)
+    rng = np.random.default_rng(3)
+    n = 40
+    z, r = rng.uniform(0.2, 0.8, n), rng.uniform(0.1, 0.4, n)
+    q, mass = -1.0, 2.0
+    s.inject(z, r, np.zeros(n), np.zeros(n), np.zeros(n), q, mass, 0.0)
+    s.step()
+    assert np.allclose(s.u[:, 2], q / mass * (-V) * dt, rtol=1e-12, atol=0)
+    assert np.abs(s.u[:, :2]).max() < 1e-12 * V * dt
+    assert np.all(s.E == 0) and np.all(s.B == 0)
