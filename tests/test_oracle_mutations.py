@@ -126,6 +126,14 @@ C_CASES = [
      "if (s < sx) { sx = s; kx = k; }",
      "if (kx < 0) { sx = s; kx = k; }",
      lambda cav: TP.test_multi_cell_current_is_the_line_integral_over_the_crossed_cells(cav)),
+    ("charge: the new position's nodes given the old lambdas",
+     "for (int k = 0; k < 3; k++) Q[nn[k]] += q_src * l[k];",
+     "for (int k = 0; k < 3; k++) Q[nn[k]] += q_src * lam[3 * p + k];",
+     lambda cav: TP.test_dce_exact_with_multi_cell_crossings(cav)),
+    ("charge at injection: each node given its neighbour's lambda",
+     "Q[tri_nodes[3 * t + k]] += q_src * lam[3 * p + k];",
+     "Q[tri_nodes[3 * t + k]] += q_src * lam[3 * p + (k + 1) % 3];",
+     lambda cav: TP.test_dce_exact_with_multi_cell_crossings(cav)),
     ("wall: the absorbed charge not booked",
      "for (int k = 0; k < 3; k++) Qabs[nn[k]] += q_src * lc[k];",
      "for (int k = 0; k < 3; k++) Qabs[nn[k]] += 0.0 * lc[k];",
@@ -183,6 +191,13 @@ PY_CASES = [
     ("stable step 1/sqrt(lambda_max)", OO, "dt_stable",
      "return 2.0 / math.sqrt(lam), lam", "return 1.0 / math.sqrt(lam), lam", (TO, OS),
      lambda cav: TO.test_dt_stable_matches_eigensolver(), None),
+    ("location: lambda over the area instead of twice the area", OP, "barycentric",
+     "/ (2.0 * mesh.area[t])", "/ mesh.area[t]", (TO,),
+     lambda cav: TP.test_locate_by_brute_force(), None),
+    ("location: one product of the signed area with swapped nodes", OP, "barycentric",
+     "lam[:, k] = ((p[:, a, 0] - z) * (p[:, b, 1] - rho)",
+     "lam[:, k] = ((p[:, b, 0] - z) * (p[:, a, 1] - rho)", (TO,),
+     lambda cav: TP.test_locate_by_brute_force(), None),
     ("cycle: B^{n+1/2} at the gather instead of the time-centred B", OS.OracleSim,
      "push_particles", "Bavg = 0.5 * (B_half + self.B)", "Bavg = B_half", (),
      lambda cav: TP.test_rotational_field_fixes_faraday_sign_and_time_centred_B(), None),

@@ -367,3 +367,34 @@ def test_multi_cell_current_is_the_line_integral_over_the_crossed_cells(cavity):
     assert np.allclose(zn, r1[:, 0], atol=1e-12) and np.allclose(rn, r1[:, 1], atol=1e-12)
     ref = sum(_path_current(m, r0[i], r1[i]) for i in range(n)) * (s.q_src / dt)
     assert np.abs(s.J - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_locate_by_brute_force():
+    """Point location (used to place injected and emitted particles): against every
+    triangle's barycentric coordinates from a linear solve, the located triangle holds
+    the point (all lambda >= -1e-12, sum 1, reproducing the point) and has the largest
+    smallest coordinate; points outside the mesh get -1.  On interior edge midpoints the
+    answer is one of the edge's two triangles."""
+    m = Mesh(*W.cavity_mesh(n_tri=300, seed=13))
+    rng = np.random.default_rng(5)
+    n = 1500
+    z = rng.uniform(-0.1, 1.1, n)
+    r = rng.uniform(0.0, 0.6, n)
+    A = np.stack([np.ones((m.N2, 3)), m.nodes[m.tris][:, :, 0], m.nodes[m.tris][:, :, 1]], 1)
+    Ainv = np.linalg.inv(A)                                   # lambda = Ainv @ (1, z, rho)
+    lam_all = np.einsum("tij,nj->nti", Ainv, np.stack([np.ones(n), z, r], 1))
+    mins = lam_all.min(2)
+    inside = mins.max(1) >= -1e-12
+    tri, lam = TPart.locate(m, z, r)
+    assert np.array_equal(tri >= 0, inside)
+    k = np.flatnonzero(inside)
+    assert np.array_equal(tri[k], np.argmax(mins[k], 1))
+    assert np.allclose(lam[k], lam_all[k, tri[k]], rtol=0, atol=1e-12)
+    assert np.allclose(lam[k].sum(1), 1.0, atol=1e-14)
+    p = m.nodes[m.tris[tri[k]]]
+    assert np.allclose(np.einsum("nk,nkd->nd", lam[k], p), np.stack([z[k], r[k]], 1), atol=1e-14)
+    inner = np.flatnonzero(m.edge_tag == 0)
+    mid = m.nodes[m.edge_nodes[inner]].mean(1)
+    tri_e, lam_e = TPart.locate(m, mid[:, 0], mid[:, 1])
+    assert np.all((tri_e == m.edge_tris[inner, 0]) | (tri_e == m.edge_tris[inner, 1]))
+    assert lam_e.min() >= -1e-12
