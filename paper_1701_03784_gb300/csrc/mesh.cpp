@@ -162,7 +162,7 @@ extern "C" const char *pic_last_error(void) { return pic::g_err.c_str(); }
 extern "C" pic_status pic_mesh_create(const double *nodes_zr, int64_t n_nodes,
                                       const int32_t *tris, int64_t n_tris,
                                       const int32_t *bedge_nodes, const int32_t *bedge_tag,
-                                      int64_t n_bedges, const pic_units *u, pic_mesh **out) {
+                                      int64_t n_bedges, const pic_units *u, pic_mesh **out) try {
     if (!nodes_zr || !tris || !u || !out || n_nodes < 3 || n_tris < 1 || n_bedges < 0 ||
         (n_bedges > 0 && (!bedge_nodes || !bedge_tag))) {
         set_error("pic_mesh_create: null pointer or bad size");
@@ -364,10 +364,11 @@ extern "C" pic_status pic_mesh_create(const double *nodes_zr, int64_t n_nodes,
     *out = pm;
     return PIC_OK;
 }
+PIC_CATCH("pic_mesh_create")
 
 extern "C" pic_status pic_mesh_info(const pic_mesh *m, int64_t *n_nodes, int64_t *n_edges,
                                     int64_t *n_tris, int64_t *n_free_edges,
-                                    int64_t *spai_nnz) {
+                                    int64_t *spai_nnz) try {
     if (!m) {
         set_error("pic_mesh_info: null mesh");
         return PIC_ERR_ARG;
@@ -379,8 +380,9 @@ extern "C" pic_status pic_mesh_info(const pic_mesh *m, int64_t *n_nodes, int64_t
     if (spai_nnz) *spai_nnz = m->h.have_spai ? (int64_t)m->h.M_val.size() : 0;
     return PIC_OK;
 }
+PIC_CATCH("pic_mesh_info")
 
-extern "C" pic_status pic_mesh_edges(const pic_mesh *m, int32_t *edge_nodes) {
+extern "C" pic_status pic_mesh_edges(const pic_mesh *m, int32_t *edge_nodes) try {
     if (!m || !edge_nodes) {
         set_error("pic_mesh_edges: null pointer");
         return PIC_ERR_ARG;
@@ -388,5 +390,6 @@ extern "C" pic_status pic_mesh_edges(const pic_mesh *m, int32_t *edge_nodes) {
     std::copy(m->h.edge_nodes.begin(), m->h.edge_nodes.end(), edge_nodes);
     return PIC_OK;
 }
+PIC_CATCH("pic_mesh_edges")
 
 extern "C" void pic_mesh_destroy(pic_mesh *m) { delete m; }

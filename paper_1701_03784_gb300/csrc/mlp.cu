@@ -353,7 +353,7 @@ struct pic_mlp {
     } while (0)
 
 extern "C" pic_status pic_mlp_create(int32_t n_members, int32_t n_layers, const int32_t *sizes,
-                                     int32_t max_batch, pic_mlp **out) {
+                                     int32_t max_batch, pic_mlp **out) try {
     if (!sizes || !out || n_members < 1 || n_members > 64 || n_layers < 1 || n_layers > 16 ||
         max_batch < 1 || max_batch > (1 << 20)) {
         set_error("pic_mlp_create: bad arguments");
@@ -376,8 +376,9 @@ extern "C" pic_status pic_mlp_create(int32_t n_members, int32_t n_layers, const 
     *out = m.release();
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_create")
 
-extern "C" pic_status pic_mlp_param_count(pic_mlp *m, int64_t *per_member) {
+extern "C" pic_status pic_mlp_param_count(pic_mlp *m, int64_t *per_member) try {
     MLP_CHECK(m, "pic_mlp_param_count");
     if (!per_member) {
         set_error("pic_mlp_param_count: null output");
@@ -386,8 +387,9 @@ extern "C" pic_status pic_mlp_param_count(pic_mlp *m, int64_t *per_member) {
     *per_member = m->impl->P;
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_param_count")
 
-extern "C" pic_status pic_mlp_params_set(pic_mlp *m, const double *params) {
+extern "C" pic_status pic_mlp_params_set(pic_mlp *m, const double *params) try {
     MLP_CHECK(m, "pic_mlp_params_set");
     MlpImpl &x = *m->impl;
     if (!params) {
@@ -404,8 +406,9 @@ extern "C" pic_status pic_mlp_params_set(pic_mlp *m, const double *params) {
     PIC_CUDA_TRY(cudaDeviceSynchronize());
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_params_set")
 
-extern "C" pic_status pic_mlp_params_get(pic_mlp *m, double *params) {
+extern "C" pic_status pic_mlp_params_get(pic_mlp *m, double *params) try {
     MLP_CHECK(m, "pic_mlp_params_get");
     MlpImpl &x = *m->impl;
     if (!params) {
@@ -418,9 +421,10 @@ extern "C" pic_status pic_mlp_params_get(pic_mlp *m, double *params) {
     for (size_t i = 0; i < h.size(); i++) params[i] = h[i];
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_params_get")
 
 extern "C" pic_status pic_mlp_grad(pic_mlp *m, const float *X, const float *T, int64_t n,
-                                   double *grads, double *loss, void *st) {
+                                   double *grads, double *loss, void *st) try {
     MLP_CHECK(m, "pic_mlp_grad");
     MlpImpl &x = *m->impl;
     if (!X || !T || !grads || n < 1 || n > x.max_batch) {
@@ -448,10 +452,11 @@ extern "C" pic_status pic_mlp_grad(pic_mlp *m, const float *X, const float *T, i
         for (int z = 0; z < x.E; z++) loss[z] = hl[z];
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_grad")
 
 extern "C" pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *T, int64_t n,
                                     int32_t batch, int64_t steps, double lr, uint64_t seed,
-                                    double *last_loss, void *st) {
+                                    double *last_loss, void *st) try {
     MLP_CHECK(m, "pic_mlp_train");
     MlpImpl &x = *m->impl;
     if (!X || !T || n < 1 || batch < 1 || batch > x.max_batch || steps < 0 || !(lr > 0)) {
@@ -491,9 +496,10 @@ extern "C" pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *T, 
     }
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_train")
 
 extern "C" pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int64_t n,
-                                      int32_t tensor_cores, void *st) {
+                                      int32_t tensor_cores, void *st) try {
     MLP_CHECK(m, "pic_mlp_forward");
     MlpImpl &x = *m->impl;
     if (!X || !Y || n < 0) {
@@ -522,8 +528,9 @@ extern "C" pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int6
     PIC_CUDA_TRY(cudaGetLastError());
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_forward")
 
-extern "C" pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores) {
+extern "C" pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores) try {
     MLP_CHECK(m, "pic_mlp_set_training");
     MlpImpl &x = *m->impl;
     if (tensor_cores && !x.tc.ok) {
@@ -533,5 +540,6 @@ extern "C" pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores) {
     x.train_tc = tensor_cores != 0;
     return PIC_OK;
 }
+PIC_CATCH("pic_mlp_set_training")
 
 extern "C" void pic_mlp_destroy(pic_mlp *m) { delete m; }

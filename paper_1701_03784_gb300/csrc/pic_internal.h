@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -18,6 +20,23 @@ namespace pic {
 // errors
 // ---------------------------------------------------------------------------------
 void set_error(const char *fmt, ...);
+
+// Handlers closing the function-try-block of every status-returning entry point, so that
+// no C++ exception (a failed host allocation, a thread that cannot start) crosses the C
+// ABI: the call returns a status and leaves its message instead.
+#define PIC_CATCH(name)                                                    \
+    catch (const std::bad_alloc &) {                                       \
+        ::pic::set_error("%s: out of host memory", name);                  \
+        return PIC_ERR_OOM;                                                \
+    }                                                                      \
+    catch (const std::exception &ex__) {                                   \
+        ::pic::set_error("%s: %s", name, ex__.what());                     \
+        return PIC_ERR_ARG;                                                \
+    }                                                                      \
+    catch (...) {                                                          \
+        ::pic::set_error("%s: unexpected error", name);                    \
+        return PIC_ERR_ARG;                                                \
+    }
 
 // device-memory hooks installed by pic_set_allocator (nulls: cudaMalloc / cudaFree)
 struct Allocator {

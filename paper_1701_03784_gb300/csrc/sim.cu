@@ -1295,7 +1295,7 @@ struct pic_sim {
         }                                                    \
     } while (0)
 
-extern "C" pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_, void *ctx) {
+extern "C" pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_, void *ctx) try {
     if ((alloc == nullptr) != (free_ == nullptr)) {
         set_error("pic_set_allocator: give both functions or neither");
         return PIC_ERR_ARG;
@@ -1306,9 +1306,10 @@ extern "C" pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_, v
     g_allocator.ctx = ctx;
     return PIC_OK;
 }
+PIC_CATCH("pic_set_allocator")
 
 extern "C" pic_status pic_sim_create(pic_mesh *pm, double dt, double bz, int64_t max_particles,
-                                     pic_sim **out) {
+                                     pic_sim **out) try {
     if (!pm || !out || !(dt > 0) || !std::isfinite(bz) || max_particles < 0 ||
         max_particles >= ((int64_t)1 << 31)) {
         set_error("pic_sim_create: bad argument");
@@ -1348,20 +1349,23 @@ extern "C" pic_status pic_sim_create(pic_mesh *pm, double dt, double bz, int64_t
     *out = s.release();
     return PIC_OK;
 }
+PIC_CATCH("pic_sim_create")
 
 extern "C" pic_status pic_sim_autotune(pic_sim *s, int32_t trial_steps, pic_tuning *out,
-                                       void *st) {
+                                       void *st) try {
     SIM_CHECK(s, "pic_sim_autotune");
     return s->impl->autotune(trial_steps, out, (cudaStream_t)st);
 }
+PIC_CATCH("pic_sim_autotune")
 
-extern "C" pic_status pic_sim_set_graph(pic_sim *s, int32_t enable) {
+extern "C" pic_status pic_sim_set_graph(pic_sim *s, int32_t enable) try {
     SIM_CHECK(s, "pic_sim_set_graph");
     s->impl->set_graph(enable != 0);
     return PIC_OK;
 }
+PIC_CATCH("pic_sim_set_graph")
 
-extern "C" pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval) {
+extern "C" pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval) try {
     SIM_CHECK(s, "pic_sim_set_sort_interval");
     if (interval < 0) {
         set_error("pic_sim_set_sort_interval: negative interval");
@@ -1370,8 +1374,9 @@ extern "C" pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval) {
     s->impl->sort_interval = interval;
     return PIC_OK;
 }
+PIC_CATCH("pic_sim_set_sort_interval")
 
-extern "C" pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher) {
+extern "C" pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher) try {
     SIM_CHECK(s, "pic_sim_set_pusher");
     if (pusher != PIC_PUSHER_BORIS && pusher != PIC_PUSHER_VAY) {
         set_error("pic_sim_set_pusher: unknown pusher %d", (int)pusher);
@@ -1380,73 +1385,85 @@ extern "C" pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher) {
     s->impl->pusher = pusher;
     return PIC_OK;
 }
+PIC_CATCH("pic_sim_set_pusher")
 
-extern "C" pic_status pic_sim_set_static_field(pic_sim *s, const double *E_static, void *st) {
+extern "C" pic_status pic_sim_set_static_field(pic_sim *s, const double *E_static, void *st) try {
     SIM_CHECK(s, "pic_sim_set_static_field");
     return s->impl->set_static_field(E_static, (cudaStream_t)st);
 }
+PIC_CATCH("pic_sim_set_static_field")
 
-extern "C" pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *st) {
+extern "C" pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *st) try {
     SIM_CHECK(s, "pic_sim_set_emitter");
     return s->impl->set_emitter(e, (cudaStream_t)st);
 }
+PIC_CATCH("pic_sim_set_emitter")
 
 extern "C" pic_status pic_sim_set_loss(pic_sim *s, const double *sigma_e, const double *sigma_m,
-                                       void *st) {
+                                       void *st) try {
     SIM_CHECK(s, "pic_sim_set_loss");
     return s->impl->set_loss(sigma_e, sigma_m, (cudaStream_t)st);
 }
+PIC_CATCH("pic_sim_set_loss")
 
 extern "C" pic_status pic_sim_set_probes(pic_sim *s, int64_t n_entries, const int32_t *face,
                                          const int32_t *group, const double *weight,
                                          int32_t n_groups, const int32_t *power,
-                                         int64_t capacity, int32_t every, void *st) {
+                                         int64_t capacity, int32_t every, void *st) try {
     SIM_CHECK(s, "pic_sim_set_probes");
     return s->impl->set_probes(n_entries, face, group, weight, n_groups, power, capacity, every,
                                (cudaStream_t)st);
 }
+PIC_CATCH("pic_sim_set_probes")
 
 extern "C" pic_status pic_probes_read(pic_sim *s, double *out, int64_t cap_records,
-                                      int64_t *n_records, int64_t *n_dropped, void *st) {
+                                      int64_t *n_records, int64_t *n_dropped, void *st) try {
     SIM_CHECK(s, "pic_probes_read");
     return s->impl->probes_read(out, cap_records, n_records, n_dropped, (cudaStream_t)st);
 }
+PIC_CATCH("pic_probes_read")
 
-extern "C" pic_status pic_fields_set(pic_sim *s, const double *E, const double *B, void *st) {
+extern "C" pic_status pic_fields_set(pic_sim *s, const double *E, const double *B, void *st) try {
     SIM_CHECK(s, "pic_fields_set");
     return s->impl->fields_set(E, B, (cudaStream_t)st);
 }
+PIC_CATCH("pic_fields_set")
 
 extern "C" pic_status pic_particles_inject(pic_sim *s, int64_t n, const double *z,
                                            const double *rho, const double *ur, const double *up,
-                                           const double *uz, double q, double m, double w, void *st) {
+                                           const double *uz, double q, double m, double w, void *st) try {
     SIM_CHECK(s, "pic_particles_inject");
     return s->impl->inject(n, z, rho, ur, up, uz, q, m, w, (cudaStream_t)st);
 }
+PIC_CATCH("pic_particles_inject")
 
-extern "C" pic_status pic_step(pic_sim *s, int64_t n, void *st) {
+extern "C" pic_status pic_step(pic_sim *s, int64_t n, void *st) try {
     SIM_CHECK(s, "pic_step");
     return s->impl->step(n, (cudaStream_t)st);
 }
+PIC_CATCH("pic_step")
 
 extern "C" pic_status pic_diagnostics(pic_sim *s, pic_diag *o, double *E, double *B, double *J,
-                                      void *st) {
+                                      void *st) try {
     SIM_CHECK(s, "pic_diagnostics");
     return s->impl->diagnostics(o, E, B, J, (cudaStream_t)st);
 }
+PIC_CATCH("pic_diagnostics")
 
 extern "C" pic_status pic_charges_get_static(pic_sim *s, double *Q, double *Qp, double *Qa,
-                                             void *st) {
+                                             void *st) try {
     SIM_CHECK(s, "pic_charges_get_static");
     return s->impl->charges_static(Q, Qp, Qa, (cudaStream_t)st);
 }
+PIC_CATCH("pic_charges_get_static")
 
-extern "C" pic_status pic_charges_get(pic_sim *s, double *Q, double *Qp, double *Qa, void *st) {
+extern "C" pic_status pic_charges_get(pic_sim *s, double *Q, double *Qp, double *Qa, void *st) try {
     SIM_CHECK(s, "pic_charges_get");
     return s->impl->charges(Q, Qp, Qa, (cudaStream_t)st);
 }
+PIC_CATCH("pic_charges_get")
 
-extern "C" pic_status pic_particles_count(pic_sim *s, int64_t *n, void *st) {
+extern "C" pic_status pic_particles_count(pic_sim *s, int64_t *n, void *st) try {
     SIM_CHECK(s, "pic_particles_count");
     if (!n) {
         set_error("pic_particles_count: null output");
@@ -1454,14 +1471,16 @@ extern "C" pic_status pic_particles_count(pic_sim *s, int64_t *n, void *st) {
     }
     return s->impl->count(n, (cudaStream_t)st);
 }
+PIC_CATCH("pic_particles_count")
 
 extern "C" pic_status pic_particles_get(pic_sim *s, int64_t cap, int64_t *pid, int32_t *tri,
-                                        double *lam, double *u, void *st) {
+                                        double *lam, double *u, void *st) try {
     SIM_CHECK(s, "pic_particles_get");
     return s->impl->get(cap, pid, tri, lam, u, (cudaStream_t)st);
 }
+PIC_CATCH("pic_particles_get")
 
-extern "C" pic_status pic_particles_raw_bytes(pic_sim *s, int64_t *b) {
+extern "C" pic_status pic_particles_raw_bytes(pic_sim *s, int64_t *b) try {
     SIM_CHECK(s, "pic_particles_raw_bytes");
     if (!b) {
         set_error("pic_particles_raw_bytes: null output");
@@ -1470,27 +1489,32 @@ extern "C" pic_status pic_particles_raw_bytes(pic_sim *s, int64_t *b) {
     *b = s->impl->raw_bytes();
     return PIC_OK;
 }
+PIC_CATCH("pic_particles_raw_bytes")
 
-extern "C" pic_status pic_particles_raw_get(pic_sim *s, void *dst, int64_t n, void *st) {
+extern "C" pic_status pic_particles_raw_get(pic_sim *s, void *dst, int64_t n, void *st) try {
     SIM_CHECK(s, "pic_particles_raw_get");
     return s->impl->raw_get(dst, n, (cudaStream_t)st);
 }
+PIC_CATCH("pic_particles_raw_get")
 
-extern "C" pic_status pic_particles_raw_set(pic_sim *s, const void *src, int64_t n, void *st) {
+extern "C" pic_status pic_particles_raw_set(pic_sim *s, const void *src, int64_t n, void *st) try {
     SIM_CHECK(s, "pic_particles_raw_set");
     return s->impl->raw_set(src, n, (cudaStream_t)st);
 }
+PIC_CATCH("pic_particles_raw_set")
 
 extern "C" pic_status pic_step_host(pic_sim *s, void *state, int64_t n_slots, int64_t n_steps,
-                                     void *st) {
+                                     void *st) try {
     SIM_CHECK(s, "pic_step_host");
     return s->impl->step_host(state, n_slots, n_steps, (cudaStream_t)st);
 }
+PIC_CATCH("pic_step_host")
 
 extern "C" pic_status pic_kernel_timing(pic_sim *s, int32_t enable, double *ms, int64_t *launches,
-                                        void *st) {
+                                        void *st) try {
     SIM_CHECK(s, "pic_kernel_timing");
     return s->impl->timing(enable, ms, launches, (cudaStream_t)st);
 }
+PIC_CATCH("pic_kernel_timing")
 
 extern "C" void pic_sim_destroy(pic_sim *s) { delete s; }

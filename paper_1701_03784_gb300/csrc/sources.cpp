@@ -199,7 +199,7 @@ using namespace pic;
 extern "C" pic_status pic_static_potential(const pic_mesh *pm, int64_t n_held,
                                            const int32_t *held_nodes, const double *held_phi,
                                            const double *charge, double *phi_out,
-                                           double *E_out) {
+                                           double *E_out) try {
     if (!pm || n_held <= 0 || !held_nodes || !held_phi) {
         set_error("pic_static_potential: bad argument");
         return PIC_ERR_ARG;
@@ -230,3 +230,4 @@ extern "C" pic_status pic_static_potential(const pic_mesh *pm, int64_t n_held,
             E_out[e] = phi[m.edge_nodes[2 * e]] - phi[m.edge_nodes[2 * e + 1]];
     return PIC_OK;
 }
+PIC_CATCH("pic_static_potential")

@@ -49,7 +49,7 @@ static void least_squares(std::vector<double> &A, int rows, int cols, std::vecto
 using namespace pic;
 
 extern "C" pic_status pic_spai_build(pic_mesh *pm, int32_t level, double drop_tol,
-                                     double *dt_stable_out) {
+                                     double *dt_stable_out) try {
     if (!pm || level < 0 || level > 8 || !(drop_tol >= 0.0 && drop_tol < 1.0)) {
         set_error("pic_spai_build: bad argument");
         return PIC_ERR_ARG;
@@ -227,9 +227,10 @@ extern "C" pic_status pic_spai_build(pic_mesh *pm, int32_t level, double drop_to
     if (dt_stable_out) *dt_stable_out = m.dt_stable;
     return PIC_OK;
 }
+PIC_CATCH("pic_spai_build")
 
 extern "C" pic_status pic_spai_get(const pic_mesh *pm, int32_t *free_edges, int64_t *indptr,
-                                   int32_t *indices, double *values) {
+                                   int32_t *indices, double *values) try {
     if (!pm || !pm->h.have_spai) {
         set_error("pic_spai_get: no SPAI built");
         return PIC_ERR_STATE;
@@ -241,9 +242,10 @@ extern "C" pic_status pic_spai_get(const pic_mesh *pm, int32_t *free_edges, int6
     if (values) std::copy(m.M_val.begin(), m.M_val.end(), values);
     return PIC_OK;
 }
+PIC_CATCH("pic_spai_get")
 
 extern "C" pic_status pic_spai_info(const pic_mesh *pm, int64_t *nnz, double *residual_rms,
-                                    double *residual_max) {
+                                    double *residual_max) try {
     if (!pm || !pm->h.have_spai) {
         set_error("pic_spai_info: no SPAI built");
         return PIC_ERR_STATE;
@@ -288,3 +290,4 @@ extern "C" pic_status pic_spai_info(const pic_mesh *pm, int64_t *nnz, double *re
     if (residual_max) *residual_max = mx;
     return PIC_OK;
 }
+PIC_CATCH("pic_spai_info")

@@ -4,6 +4,7 @@ the oracle.  No GPU needed: these calls do not touch the device."""
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -110,3 +111,42 @@ def test_header_is_plain_c():
     r = subprocess.run([gcc, "-std=c99", "-fsyntax-only", "-Wall", "-Werror", "-x", "c", hdr],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+_OOM_CHILD = r'''
+import resource, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_1701_03784_gb300 import pic as P
+
+n = 600                                  # structured grid: 720k triangles
+z, r = np.meshgrid(np.linspace(0, 1, n + 1), np.linspace(0, 1, n + 1), indexing="ij")
+nodes = np.stack([z.ravel(), r.ravel()], 1)
+idx = lambda i, j: i * (n + 1) + j
+i, j = [a.ravel() for a in np.meshgrid(np.arange(n), np.arange(n), indexing="ij")]
+tris = np.concatenate([np.stack([idx(i, j), idx(i + 1, j), idx(i + 1, j + 1)], 1),
+                       np.stack([idx(i, j), idx(i + 1, j + 1), idx(i, j + 1)], 1)])
+k = np.arange(n)
+be = np.concatenate([np.stack([idx(k, 0), idx(k + 1, 0)], 1), np.stack([idx(k, n), idx(k + 1, n)], 1),
+                     np.stack([idx(0, k), idx(0, k + 1)], 1), np.stack([idx(n, k), idx(n, k + 1)], 1)])
+bt = np.concatenate([np.full(n, P.PIC_BC_AXIS), np.full(3 * n, P.PIC_BC_PEC)])
+vm = int([l for l in open("/proc/self/status") if l.startswith("VmSize")][0].split()[1])
+resource.setrlimit(resource.RLIMIT_AS, (vm * 1024 + 32 * 2 ** 20, resource.RLIM_INFINITY))
+try:
+    P.pic_mesh_create(nodes, tris, be, bt)
+    print("created")
+except P.PicError as e:
+    print("status:", e)
+'''
+
+
+def test_host_allocation_failure_returns_a_status(pic, tmp_path):
+    """Every call returns a status and never aborts: with the address space capped just
+    above what the process holds, building a 720k-triangle mesh runs out of host memory
+    inside the library, and the call reports PIC_ERR_OOM instead of ending the process."""
+    script = tmp_path / "oom_child.py"
+    script.write_text(_OOM_CHILD)
+    out = subprocess.run([sys.executable, str(script), ROOT], capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert "PIC_ERR_OOM" in out.stdout and "out of host memory" in out.stdout, out.stdout
