@@ -77,3 +77,22 @@ def test_stability_limit(cavity):
 
     assert run(0.5, 1000) < 2.0
     assert run(1.2, 400) > 1e6
+
+
+def test_field_energy_of_uniform_fields_closed_form():
+    """The energy densities eps0 E^2 / 2 and B^2 / (2 mu0) integrated per radian
+    (int rho dz drho = a^2 L / 2 over the cavity): a uniform E (exact in Whitney 1-forms)
+    and a uniform B_phi (B_f = B0 A_f) must give eps0 E0^2 a^2 L / 4 and
+    B0^2 a^2 L / (4 mu0), for any eps0 and mu0."""
+    from oracle.operators import Mesh, hodge_eps, hodge_mu_inv, field_energy
+    a, L = 0.5, 1.0
+    m = Mesh(*W.cavity_mesh(a=a, L=L, n_tri=600, seed=4))
+    eps0, mu0 = 2.5, 0.6
+    se, mi = hodge_eps(m, eps0), hodge_mu_inv(m, mu0)
+    d = m.nodes[m.edge_nodes[:, 1]] - m.nodes[m.edge_nodes[:, 0]]
+    E0, B0 = 0.7, 1.3
+    for comp in (0, 1):
+        We = field_energy(m, se, mi, E0 * d[:, comp], np.zeros(m.N2))
+        assert abs(We - eps0 * E0 ** 2 * a * a * L / 4) < 1e-12 * We
+    Wm = field_energy(m, se, mi, np.zeros(m.N1), B0 * m.area)
+    assert abs(Wm - B0 ** 2 * a * a * L / (4 * mu0)) < 1e-12 * Wm

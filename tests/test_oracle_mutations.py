@@ -29,6 +29,7 @@ TU = importlib.import_module("test_oracle_pushers")
 TS = importlib.import_module("test_oracle_sources")
 TM = importlib.import_module("test_oracle_mlp")
 TL = importlib.import_module("test_oracle_layer")
+TF = importlib.import_module("test_oracle_fields")
 
 
 def _patch_py(monkeypatch, owner, name, old, new, importers=()):
@@ -198,6 +199,24 @@ PY_CASES = [
      "lam[:, k] = ((p[:, a, 0] - z) * (p[:, b, 1] - rho)",
      "lam[:, k] = ((p[:, b, 0] - z) * (p[:, a, 1] - rho)", (TO,),
      lambda cav: TP.test_locate_by_brute_force(), None),
+    ("SPAI: one hop more than the pattern level", OO, "spai_pattern",
+     "for _ in range(level):", "for _ in range(level + 1):", (),
+     lambda cav: TO.test_spai_level0_closed_form(), None),
+    ("stable step: curl-curl operator without star_mu^-1", OO, "curl_curl",
+     "return (Dc.T @ sp.diags(mu_inv) @ Dc).tocsr()", "return (Dc.T @ Dc).tocsr()", (TO,),
+     lambda cav: TF.test_stability_limit(OracleSim(*W.cavity_mesh())), None),
+    ("field energy: magnetic part without the 1/2", OO, "field_energy",
+     "0.5 * np.sum(mu_inv * B * B)", "np.sum(mu_inv * B * B)", (OS,),
+     lambda cav: TF.test_field_energy_of_uniform_fields_closed_form(), None),
+    ("field energy: electric part without star_eps", OO, "field_energy",
+     "0.5 * E @ (star_eps @ E)", "0.5 * E @ E", (OS,),
+     lambda cav: TF.test_field_energy_of_uniform_fields_closed_form(), None),
+    ("kinetic energy: gamma m c^2 instead of (gamma - 1) m c^2", OS.OracleSim,
+     "kinetic_energy", "np.sum((gam - 1.0))", "np.sum(gam)", (),
+     lambda cav: TP.test_kinetic_energy_limits(cav), None),
+    ("kinetic energy: the macro-particle weight left out", OS.OracleSim, "kinetic_energy",
+     "* self.mass * self.weight * self.c ** 2", "* self.mass * self.c ** 2", (),
+     lambda cav: TP.test_kinetic_energy_limits(cav), None),
     ("cycle: B^{n+1/2} at the gather instead of the time-centred B", OS.OracleSim,
      "push_particles", "Bavg = 0.5 * (B_half + self.B)", "Bavg = B_half", (),
      lambda cav: TP.test_rotational_field_fixes_faraday_sign_and_time_centred_B(), None),

@@ -398,3 +398,16 @@ def test_locate_by_brute_force():
     tri_e, lam_e = TPart.locate(m, mid[:, 0], mid[:, 1])
     assert np.all((tri_e == m.edge_tris[inner, 0]) | (tri_e == m.edge_tris[inner, 1]))
     assert lam_e.min() >= -1e-12
+
+
+def test_kinetic_energy_limits(cavity):
+    """Kinetic energy of the macro-particles: zero at rest, w m u^2 / 2 for u << c and
+    w m c |u| for u >> c (per macro-particle of weight w; c = 1 here)."""
+    z, r, *_ = W.uniform_in_mesh(cavity.mesh.nodes, cavity.mesh.tris, 1, 2)
+    w, mass = 3e-3, 2.0
+    for u, expect, tol in ((0.0, 0.0, 0.0), (1e-4, w * mass * 1e-8 / 2, 1e-6),
+                           (1e4, w * mass * 1e4, 1e-4)):
+        s = _fresh(cavity)
+        s.create(0.5 * s.dt_max)
+        s.inject(z, r, [0.0], [u], [0.0], -1.0, mass, w)
+        assert abs(s.kinetic_energy() - expect) <= tol * expect
