@@ -150,3 +150,26 @@ def test_host_allocation_failure_returns_a_status(pic, tmp_path):
                          timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert "PIC_ERR_OOM" in out.stdout and "out of host memory" in out.stdout, out.stdout
+
+
+def test_host_faults_are_statuses(pic):
+    """Faults injected on the host come back as statuses before any device work: a time
+    step above the SPAI-stable limit (PIC_ERR_UNSTABLE), non-finite or non-positive steps
+    and bad sizes (PIC_ERR_ARG), and SPAI parameters out of range."""
+    nodes, tris, be, bt = W.cavity_mesh(n_tri=300, seed=3)
+    m = pic.pic_mesh_create(nodes, tris, be, bt)
+    for level, tol in ((-1, 1e-4), (9, 1e-4), (2, -1e-4), (2, float("nan")), (2, 1.0)):
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_spai_build(m, level, tol)
+        assert e.value.status == pic.PIC_ERR_ARG
+    dt = pic.pic_spai_build(m, 2, 1e-4)
+    for bad_dt in (1.01 * dt, float("inf")):
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_sim_create(m, bad_dt, torch_memory=False)
+        assert e.value.status == pic.PIC_ERR_UNSTABLE and "stable" in pic.pic_last_error()
+    for args in ((0.0, 0.0, 10), (-dt, 0.0, 10), (float("nan"), 0.0, 10),
+                 (0.5 * dt, float("inf"), 10), (0.5 * dt, float("nan"), 10),
+                 (0.5 * dt, 0.0, -1), (0.5 * dt, 0.0, 1 << 31)):
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_sim_create(m, args[0], args[1], args[2], torch_memory=False)
+        assert e.value.status == pic.PIC_ERR_ARG
