@@ -130,6 +130,9 @@ k = np.arange(n)
 be = np.concatenate([np.stack([idx(k, 0), idx(k + 1, 0)], 1), np.stack([idx(k, n), idx(k + 1, n)], 1),
                      np.stack([idx(0, k), idx(0, k + 1)], 1), np.stack([idx(n, k), idx(n, k + 1)], 1)])
 bt = np.concatenate([np.full(n, P.PIC_BC_AXIS), np.full(3 * n, P.PIC_BC_PEC)])
+# in the binding's types already, so that only the library allocates under the cap
+nodes, tris = np.ascontiguousarray(nodes, np.float64), np.ascontiguousarray(tris, np.int32)
+be, bt = np.ascontiguousarray(be, np.int32), np.ascontiguousarray(bt, np.int32)
 vm = int([l for l in open("/proc/self/status") if l.startswith("VmSize")][0].split()[1])
 resource.setrlimit(resource.RLIMIT_AS, (vm * 1024 + 32 * 2 ** 20, resource.RLIM_INFINITY))
 try:
