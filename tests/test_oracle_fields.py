@@ -96,3 +96,28 @@ def test_field_energy_of_uniform_fields_closed_form():
         assert abs(We - eps0 * E0 ** 2 * a * a * L / 4) < 1e-12 * We
     Wm = field_energy(m, se, mi, np.zeros(m.N1), B0 * m.area)
     assert abs(Wm - B0 ** 2 * a * a * L / (4 * mu0)) < 1e-12 * Wm
+
+
+def test_conducting_walls_short_the_tangential_field():
+    """A uniform E_z set in a closed conducting cavity: the walls hold no tangential E
+    (on their edges E = 0, at every step), so the field is not curl-free next to them.
+    Its circulation then lives only on faces that touch a wall (every face along the tube
+    wall, whose edges run along z), and the first B half step is zero everywhere else;
+    the field oscillates instead of staying put."""
+    from oracle.operators import BC_PEC
+    s = OracleSim(*W.cavity_mesh(n_tri=800, seed=11))
+    m = s.mesh
+    s.create(0.5 * s.dt_max)
+    d = m.nodes[m.edge_nodes[:, 1]] - m.nodes[m.edge_nodes[:, 0]]
+    E0 = 0.3
+    s.set_fields(E0 * d[:, 0], np.zeros(m.N2))
+    wall = m.edge_tag == BC_PEC
+    touches = np.any(wall[m.tri_edges], axis=1)
+    shorted = np.any((wall & (np.abs(d[:, 0]) > 0))[m.tri_edges], axis=1)   # the tube wall
+    Bh = s.field_b_half()
+    assert np.abs(Bh[~touches]).max() < 1e-14 * E0
+    assert np.abs(Bh[shorted]).min() > 0.0
+    for _ in range(50):
+        s.step()
+        assert np.all(s.E[wall] == 0.0)
+    assert np.abs(s.B).max() > 1e-3 * E0

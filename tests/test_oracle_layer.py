@@ -67,3 +67,31 @@ def test_graded_layer_absorbs_a_guided_pulse(guide):
         left[layer] = s.field_energy() / e0
     assert left[False] > 0.95
     assert left[True] < 0.01
+
+
+def test_matched_uniform_conductor_scales_the_lossless_run():
+    """With the same s = sigma dt / (2 eps0) = sigma* dt / (2 mu0) on every edge and face
+    and no current, substituting E^n = r^n E'^n, B^{n+1/2} = r^{n+1/2} B'^{n+1/2}, with
+    r = (1 - s)/(1 + s), turns the time-centred lossy updates into the lossless leapfrog
+    for (E', B') with the step dt / sqrt(1 - s^2).  So the lossy run equals r^n times a
+    lossless run with that step, at every edge and step, to round-off: this fixes the
+    decay factor and the 1/(1 + s) on both increments."""
+    nodes, tris, be, bt = W.cavity_mesh(n_tri=600, seed=8)
+    o = OracleSim(nodes, tris, be, bt, eps0=1.3, mu0=0.8)
+    m = o.mesh
+    E0 = W.random_edge_values(m.N1, 1.0, 4)
+    dt = 0.5 * o.dt_max
+    s = 0.02
+    sigma_e, sigma_m = 2 * s * o.eps0 / dt, 2 * s * o.mu0 / dt
+    lossy, plain = _copy(o), _copy(o)
+    lossy.create(dt)
+    plain.create(dt / np.sqrt(1 - s * s))
+    for x in (lossy, plain):
+        x.set_fields(E0, np.zeros(m.N2))
+    lossy.set_loss(np.full(m.N1, sigma_e), np.full(m.N2, sigma_m))
+    r = (1 - s) / (1 + s)
+    for n in range(1, 61):
+        lossy.step()
+        plain.step()
+        assert np.abs(lossy.E - r ** n * plain.E).max() <= 1e-12 * np.abs(E0).max()
+        assert np.abs(lossy.B - r ** (n - 0.5) * plain.B).max() <= 1e-12 * np.abs(plain.B).max()

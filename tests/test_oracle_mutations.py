@@ -217,6 +217,41 @@ PY_CASES = [
     ("kinetic energy: the macro-particle weight left out", OS.OracleSim, "kinetic_energy",
      "* self.mass * self.weight * self.c ** 2", "* self.mass * self.c ** 2", (),
      lambda cav: TP.test_kinetic_energy_limits(cav), None),
+    ("mesh: each triangle its own neighbour across an interior edge", OO.Mesh, "__init__",
+     "self.nbr[et[both, 0], el[both, 0]] = et[both, 1]",
+     "self.nbr[et[both, 0], el[both, 0]] = et[both, 0]", (),
+     lambda cav: TP.test_walk_reaches_the_straight_line_endpoint(
+         OracleSim(*W.cavity_mesh(n_tri=800, seed=11))), None),
+    ("star_eps: local blocks assembled with rows for columns", OO, "hodge_eps",
+     "c = np.tile(mesh.tri_edges, (1, 3)).ravel()",
+     "c = np.repeat(mesh.tri_edges, 3, axis=1).ravel()", (TO, OS),
+     lambda cav: TO.test_hodge_spd(), None),
+    ("fields: tangential E kept on conductor edges", OS.OracleSim, "set_fields",
+     "E[self.mesh.edge_tag == 1] = 0.0", "pass", (),
+     lambda cav: TF.test_conducting_walls_short_the_tangential_field(), None),
+    ("Gauss law: conductor nodes not left out", OS.OracleSim, "dgl_residual",
+     "res[m.node_on_pec] = 0.0", "pass", (),
+     lambda cav: TP.test_dgl_residual_constant(cav), None),
+    ("layer: E increment without the 1/(1 + s)", OS.OracleSim, "field_e",
+     "self.E[f] = a * self.E[f] + b * inc", "self.E[f] = a * self.E[f] + inc", (),
+     lambda cav: TL.test_matched_uniform_conductor_scales_the_lossless_run(), None),
+    ("layer: B increment without the 1/(1 + s)", OS.OracleSim, "field_b_half",
+     "return a * self.B + b * inc", "return a * self.B + inc", (),
+     lambda cav: TL.test_matched_uniform_conductor_scales_the_lossless_run(), None),
+    ("emission: ids restart every step", OS.OracleSim, "emit",
+     'pids = np.arange(len(self.tri), len(self.tri) + em["per_step"])',
+     'pids = np.arange(em["per_step"])', (),
+     lambda cav: TS.test_successive_emissions_continue_the_particle_ids(), None),
+    ("draws: the half step dropped (0 becomes a possible draw)", OSrc, "uniforms",
+     ".astype(np.float64) + 0.5) * 2.0 ** -53", ".astype(np.float64)) * 2.0 ** -53", (),
+     lambda cav: TS.test_uniform_draws_stay_inside_the_open_interval_at_the_extremes(), None),
+    ("emission: cosine for both transverse momenta", OSrc, "emitted",
+     "up = u_thermal * r1 * np.sin(2.0 * math.pi * u[:, 2])",
+     "up = u_thermal * r1 * np.cos(2.0 * math.pi * u[:, 2])", (),
+     lambda cav: TS.test_emitted_transverse_momenta_are_independent_normals(), None),
+    ("static field: node charge with the wrong sign", OSrc, "static_potential",
+     "rhs = rhs + np.asarray(charge, float)[free]", "rhs = rhs - np.asarray(charge, float)[free]", (),
+     lambda cav: TS.test_gauss_law_of_a_charged_shell_fixes_the_ring_normalisation(), None),
     ("cycle: B^{n+1/2} at the gather instead of the time-centred B", OS.OracleSim,
      "push_particles", "Bavg = 0.5 * (B_half + self.B)", "Bavg = B_half", (),
      lambda cav: TP.test_rotational_field_fixes_faraday_sign_and_time_centred_B(), None),

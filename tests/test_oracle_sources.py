@@ -177,3 +177,56 @@ def test_static_field_drives_particles_but_not_the_leapfrog():
     assert np.allclose(s.u[:, 2], q / mass * (-V) * dt, rtol=1e-12, atol=0)
     assert np.abs(s.u[:, :2]).max() < 1e-12 * V * dt
     assert np.all(s.E == 0) and np.all(s.B == 0)
+
+
+def _unmix(y):
+    """Inverse of the splitmix64 output function (each xor-shift and odd multiplier is a
+    bijection of 64-bit words), so that a state with a chosen output can be built."""
+    M = 2 ** 64
+
+    def unshift(v, s):
+        x = v
+        for _ in range(64 // s + 1):
+            x = v ^ (x >> s)
+        return x
+
+    z = unshift(y, 31)
+    z = (z * pow(0x94D049BB133111EB, -1, M)) % M
+    z = unshift(z, 27)
+    z = (z * pow(0xBF58476D1CE4E5B9, -1, M)) % M
+    z = unshift(z, 30)
+    return (z - 0x9E3779B97F4A7C15) % M
+
+
+def test_uniform_draws_stay_inside_the_open_interval_at_the_extremes():
+    """The generator's smallest and largest outputs (0 and 2^64 - 1, reached from states
+    built by inverting it) map to 2^-54 and 1 - 2^-54: the draws never reach 0, whose
+    logarithm the Box-Muller step takes, nor 1."""
+    for out, u in ((0, 2.0 ** -54), (2 ** 64 - 1, 1.0 - 2.0 ** -54)):
+        x = _unmix(out)
+        assert int(S.splitmix64(np.array([x], np.uint64))[0]) == out
+        assert S.uniforms(x, np.array([0]), 1)[0, 0] == u
+
+
+def test_emitted_transverse_momenta_are_independent_normals():
+    """Box-Muller pairs: u_rho and u_phi are independent, so (u_rho^2 + u_phi^2) / (2 s^2)
+    follows the unit exponential law and their correlation vanishes."""
+    sig = 0.1
+    _, _, ur, up, _ = S.emitted(0.3, 0.2, 0.5, 2.0, sig, 7, np.arange(40000))
+    assert stats.kstest((ur ** 2 + up ** 2) / (2 * sig ** 2), "expon").pvalue > 1e-3
+    assert abs(np.corrcoef(ur, up)[0, 1]) < 0.03
+
+
+def test_successive_emissions_continue_the_particle_ids():
+    """Each step's births are new particles: their ids continue the count, so two steps
+    emit different draws, each the draws of its own ids."""
+    nodes, tris, be, bt = W.cavity_mesh(a=0.5, L=1.0, n_tri=400, seed=7)
+    s = OracleSim(nodes, tris, be, bt)
+    s.create(0.5 * s.dt_max)
+    s.set_emitter(0.02, 0.0, 0.3, 50, 1.0, 0.2, 5, -1.0, 1.0, 1e-3)
+    s.emit()
+    s.emit()
+    for k in (0, 1):
+        _, r, ur, up, uz = S.emitted(0.02, 0.0, 0.3, 1.0, 0.2, 5, np.arange(50 * k, 50 * k + 50))
+        assert np.array_equal(s.u[50 * k:50 * k + 50], np.stack([ur, up, uz], 1))
+    assert not np.any(np.isin(s.u[:50, 0], s.u[50:, 0]))
