@@ -135,6 +135,18 @@ C_CASES = [
      "Q[tri_nodes[3 * t + k]] += q_src * lam[3 * p + k];",
      "Q[tri_nodes[3 * t + k]] += q_src * lam[3 * p + (k + 1) % 3];",
      lambda cav: TP.test_dce_exact_with_multi_cell_crossings(cav)),
+    ("walk: no cap on the crossings of one step",
+     "if (nb < 0 || ncross + 1 >= max_cross) {",
+     "if (nb < 0) {",
+     lambda cav: TP.test_walk_cap_removes_the_particle_and_books_its_charge(cav)),
+    ("walk: the rest of the displacement scaled by s, not 1 - s",
+     "d[0] *= (1.0 - sx);",
+     "d[0] *= sx;",
+     lambda cav: TP.test_walk_reaches_the_straight_line_endpoint(cav)),
+    ("edges: tail and head taken the other way round",
+     "if (nodes3[i] < nodes3[j]) { *a = i; *b = j; }",
+     "if (nodes3[i] > nodes3[j]) { *a = i; *b = j; }",
+     lambda cav: TP.test_uniform_E_kick(cav, 0)),
     ("wall: the absorbed charge not booked",
      "for (int k = 0; k < 3; k++) Qabs[nn[k]] += q_src * lc[k];",
      "for (int k = 0; k < 3; k++) Qabs[nn[k]] += 0.0 * lc[k];",

@@ -411,3 +411,27 @@ def test_kinetic_energy_limits(cavity):
         s.create(0.5 * s.dt_max)
         s.inject(z, r, [0.0], [u], [0.0], -1.0, mass, w)
         assert abs(s.kinetic_energy() - expect) <= tol * expect
+
+
+def test_walk_cap_removes_the_particle_and_books_its_charge(cavity):
+    """A particle whose step crosses more cells than the walk cap (16 crossings) is taken
+    out where the cap is reached: it counts as a walk-cap overflow, its charge is booked
+    as removed at that point, and Eq. DCE holds with that sink.  A slower particle on the
+    same line, crossing fewer cells, arrives."""
+    out = {}
+    for frac in (0.9, 0.05):
+        s = _fresh(cavity)
+        s.create(0.5 * s.dt_max)
+        dt = s.dt = 1.0                       # particle-only step; the fields stay zero
+        v = frac * 0.8 / dt                   # along z across most of the cavity
+        gam = 1.0 / math.sqrt(1.0 - v * v)
+        s.inject([0.1], [0.23], [0.0], [0.0], [gam * v], -1.0, 1.0, 1e-3)
+        Qn = s.push_particles(s.field_b_half())
+        s.Q_prev, s.Q = s.Q, Qn
+        out[frac] = (s.tri[0], s.counters.copy())
+        assert np.abs(s.dce_residual()).max() * dt < 1e-15
+        if frac == 0.9:
+            assert abs(s.Qabs.sum() - s.q_src) < 1e-15 and np.all(Qn == 0)
+    assert out[0.9][0] == -1 and out[0.9][1][0] == 1 and out[0.9][1][1] == 1
+    assert out[0.9][1][2] == TPart.WALK_CAP
+    assert out[0.05][0] >= 0 and out[0.05][1][1] == 0 and 0 < out[0.05][1][2] < TPart.WALK_CAP
