@@ -317,6 +317,15 @@ PY_CASES = [
     ("network: activation after the output layer", OM, "forward",
      "a = gelu(z) if l < L - 1 else z", "a = gelu(z)", (),
      lambda cav: TM.test_single_layer_is_the_affine_map(), None),
+    ("Adam: no bias correction of the second moment", OM, "adam",
+     "vh = vv / (1 - b2 ** step)", "vh = vv", (),
+     lambda cav: TM.test_adam_first_step_is_signed_learning_rate(), None),
+    ("Adam: first moment without the (1 - b1) weight", OM, "adam",
+     "mm += (1 - b1) * g", "mm += g", (),
+     lambda cav: TM.test_adam_first_step_is_signed_learning_rate(), None),
+    ("network: loss summed instead of averaged", OM, "loss",
+     "return np.mean((y - t) ** 2)", "return np.sum((y - t) ** 2)", (),
+     lambda cav: TM.test_backward_matches_finite_differences(), None),
     ("Adam: no bias correction of the first moment", OM, "adam",
      "mh = mm / (1 - b1 ** step)", "mh = mm", (),
      lambda cav: TM.test_adam_first_step_is_signed_learning_rate(), None),
