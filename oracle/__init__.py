@@ -17,8 +17,11 @@ Layout:
   sim.py        one PIC cycle in the order of Sec. 3 (field, gather, push, scatter).
   sources.py    static gun field (Laplace problem), cathode emission with counter-based
                 draws, planar space-charge-limited current (Secs. 5.2, 5.3).
+  mlp.py        the surrogate network: forward, backward and Adam, written out plainly.
 
-Every function's pin (what fixes it other than itself) is listed in tests/test_oracle_*.py.
+Every function's pin (what fixes it other than itself) is in tests/test_oracle_*.py;
+tests/test_oracle_mutations.py plants one mistake at a time in a copy of a routine here
+and checks that its pin fails.
 """
 from .operators import Mesh, hodge_eps, hodge_mu_inv, spai, dt_stable, field_energy  # noqa: F401
 from .sim import OracleSim  # noqa: F401
