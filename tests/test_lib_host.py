@@ -176,3 +176,21 @@ def test_host_faults_are_statuses(pic):
         with pytest.raises(pic.PicError) as e:
             pic.pic_sim_create(m, args[0], args[1], args[2], torch_memory=False)
         assert e.value.status == pic.PIC_ERR_ARG
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No fallback: a copy of the Python package without the built library refuses to
+    import its binding."""
+    import shutil
+    pkg = tmp_path / "paper_1701_03784_gb300"
+    pkg.mkdir()
+    src = os.path.join(ROOT, "paper_1701_03784_gb300")
+    for f in os.listdir(src):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(src, f), pkg / f)
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n    import paper_1701_03784_gb300.pic\nexcept ImportError as e:\n"
+            "    print('refused:', e)\n" % str(tmp_path))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         timeout=120, cwd=str(tmp_path))
+    assert out.returncode == 0 and "refused: libpic_gb300.so is not built" in out.stdout, out
