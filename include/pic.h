@@ -105,7 +105,9 @@ typedef struct {
 
 /* Allocator hook for device memory (e.g. a framework's caching allocator).  alloc must
  * return device memory of at least `bytes` bytes aligned to 256 bytes, or NULL; free
- * releases it.  Install before creating simulations; pass NULLs to restore cudaMalloc. */
+ * releases it.  Install before creating simulations (each keeps the hooks it was created
+ * with); pass NULLs to restore cudaMalloc.  Not an operation of the paper.  Errors: ARG
+ * (one function given without the other). */
 typedef void *(*pic_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*pic_free_fn)(void *ptr, void *ctx);
 pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_, void *ctx);
@@ -127,11 +129,12 @@ pic_status pic_mesh_create(const double *nodes_zr, int64_t n_nodes, const int32_
                            pic_mesh **out);
 
 /* Sizes: nodes N0, edges N1, faces N2, free (non-PEC) edges, nonzeros of M (0 before
- * pic_spai_build).  Any pointer may be NULL. */
+ * pic_spai_build).  Any output pointer may be NULL.  Host-only.  Errors: ARG (null mesh). */
 pic_status pic_mesh_info(const pic_mesh *m, int64_t *n_nodes, int64_t *n_edges,
                          int64_t *n_tris, int64_t *n_free_edges, int64_t *spai_nnz);
 
-/* Edge list in library numbering: n_edges x 2 node indices (tail, head). */
+/* Edge list in library numbering (App. D: tail = lower node index): n_edges x 2 node
+ * indices (tail, head) into a caller-owned array.  Host-only.  Errors: ARG (null). */
 pic_status pic_mesh_edges(const pic_mesh *m, int32_t *edge_nodes);
 
 /* SPAI of star_eps (Sec. 3.1: the explicit, local E update).  Column j of M minimises
@@ -144,8 +147,9 @@ pic_status pic_mesh_edges(const pic_mesh *m, int32_t *edge_nodes);
 pic_status pic_spai_build(pic_mesh *m, int32_t pattern_level, double drop_tol,
                           double *dt_stable_out);
 
-/* Optional: export the free-edge numbering and M in CSR (free-edge indices).
- * free_edges: n_free entries (may be NULL); indptr: n_free+1; indices, values: nnz. */
+/* Optional: export the free-edge numbering and M in CSR (free-edge indices), into
+ * caller-owned arrays sized by pic_mesh_info.  free_edges: n_free entries (may be NULL);
+ * indptr: n_free+1; indices, values: nnz.  Host-only.  Errors: ARG, STATE (no SPAI). */
 pic_status pic_spai_get(const pic_mesh *m, int32_t *free_edges, int64_t *indptr,
                         int32_t *indices, double *values);
 
@@ -165,7 +169,9 @@ pic_status pic_spai_info(const pic_mesh *m, int64_t *nnz, double *residual_rms,
 pic_status pic_sim_create(pic_mesh *m, double dt, double bz_guide, int64_t max_particles,
                           pic_sim **out);
 
-/* Steps between particle re-sorts by triangle (default 16; 0 disables re-sorting). */
+/* Steps between particle re-sorts by triangle (default 16; 0 disables re-sorting).  Not
+ * an operation of the paper: it keeps the particles of a triangle together in memory.
+ * Errors: ARG (null handle, negative interval). */
 pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
 
 /* Velocity update of Eq. DLE (Sec. 3.3 adopts a corrected Boris scheme, citing Vay 2008).
@@ -283,8 +289,11 @@ typedef struct {
 pic_status pic_sim_autotune(pic_sim *s, int32_t trial_steps, pic_tuning *out,
                             void *cuda_stream);
 
-/* Set E^n (N1 doubles; PEC entries are forced to 0) and B^{n-1/2} (N2 doubles); either
- * may be NULL to leave it.  Resets the DGL auxiliary flux D = star_eps E. */
+/* Set E^n (N1 doubles: Whitney-1 edge values, line integrals along each edge's tail ->
+ * head; PEC entries are forced to 0, Sec. 5.1) and B^{n-1/2} (N2 doubles: Whitney-2 face
+ * fluxes) from caller-owned host arrays, copied; either may be NULL to leave it.  Resets
+ * the Gauss-law auxiliary flux D = star_eps E (Sec. 3.5.2) and its reference.  Errors: ARG
+ * (null handle), CUDA. */
 pic_status pic_fields_set(pic_sim *s, const double *E_edges, const double *B_faces_half,
                           void *cuda_stream);
 
@@ -300,13 +309,24 @@ pic_status pic_particles_inject(pic_sim *s, int64_t n, const double *z, const do
                                 const double *u_rho, const double *u_phi, const double *u_z,
                                 double q, double m, double weight, void *cuda_stream);
 
-/* Advance n_steps full cycles on the stream (asynchronous: returns once enqueued). */
+/* Advance n_steps full cycles of Sec. 3 on the stream, each in the order
+ *   emission (if set) -> B^{n+1/2} (Eq. full_d_dfl) and the per-triangle field records
+ *   -> gather, push (Eqs. DNE, DLE), walk and scatter of J^{n+1/2} (Eq. current) and
+ *   Q^{n+1} (Eq. charge) -> E^{n+1} (Eq. full_d_dal, SPAI M) -> re-sort every
+ *   sort_interval steps (an implementation step: particles ordered by triangle).
+ * Asynchronous: returns once the work is enqueued; the state stays on the device.
+ * n_steps = 0 enqueues nothing.  A bounded device wait that gives up (a stalled copy
+ * pipeline) is counted on the device and reported as PIC_ERR_TIMEOUT by the next
+ * pic_diagnostics.  Errors: ARG (null handle, n_steps < 0), CUDA (a launch or graph
+ * call failed). */
 pic_status pic_step(pic_sim *s, int64_t n_steps, void *cuda_stream);
 
 /* Synchronous diagnostics (Sec. 3.5, Sec. 5.1.1) and optional field read-back:
  * E_out (N1), B_out (N2, B^{n-1/2}), J_out (N1, J^{n-1/2} of the last step in physical
- * units), each may be NULL.  out may be NULL too: no reductions run, only the requested
- * arrays are copied (a plain field read-back). */
+ * units), each a caller-owned host array or NULL.  out may be NULL too: no reductions
+ * run, only the requested arrays are copied (a plain field read-back).  The reductions
+ * run on the device.  Errors: ARG (null handle), TIMEOUT (a bounded device wait of an
+ * earlier step gave up: the state is invalid), OOM, CUDA. */
 pic_status pic_diagnostics(pic_sim *s, pic_diag *out, double *E_out, double *B_out,
                            double *J_out, void *cuda_stream);
 
