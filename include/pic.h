@@ -398,7 +398,11 @@ pic_status pic_kernel_timing(pic_sim *s, int32_t enable, double *push_ms, int64_
  * where the members agree (the caller gates on their spread).  Parameters per member: for
  * each layer W (n_out x n_in, row-major) then b (n_out), members one after another.
  * Device memory comes from the allocator hook, like the simulations'.  max_batch bounds
- * the training batch and the rows of pic_mlp_grad; inference is chunked. */
+ * the training batch and the rows of pic_mlp_grad; inference is chunked.  Limits:
+ * 1..64 members, 1..16 layers, widths 1..4096, max_batch 1..2^20.  Host arrays are
+ * caller-owned and copied; device arrays (X, T, Y) are caller-owned CUDA memory on the
+ * network's device.  Errors of every call: ARG (null handle or pointer, a limit above),
+ * OOM, CUDA, and TIMEOUT where stated; pic_mlp_destroy releases everything. */
 typedef struct pic_mlp pic_mlp;
 pic_status pic_mlp_create(int32_t n_members, int32_t n_layers, const int32_t *sizes,
                           int32_t max_batch, pic_mlp **out);
@@ -434,8 +438,12 @@ pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int64_t n, int3
 pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores);
 void pic_mlp_destroy(pic_mlp *m);
 
+/* Release a simulation (its device memory included) or a mesh; NULL is ignored.  A mesh
+ * must outlive the simulations made from it. */
 void pic_sim_destroy(pic_sim *s);
 void pic_mesh_destroy(pic_mesh *m);
+/* Message of the last failing call on this thread (empty if none); valid until the next
+ * failing call on the same thread. */
 const char *pic_last_error(void);
 
 #ifdef __cplusplus
