@@ -87,6 +87,18 @@ C_CASES = [
      "double Bf[3] = {0.0, Bavg[t] / area[t], bz};",
      "double Bf[3] = {0.0, Bavg[t], bz};",
      lambda cav: TP.test_rotational_field_fixes_faraday_sign_and_time_centred_B()),
+    ("gather: E_rho with the wrong sign",
+     "er += Ee * (lam[a] * g[2 * b + 1] - lam[b] * g[2 * a + 1]);",
+     "er -= Ee * (lam[a] * g[2 * b + 1] - lam[b] * g[2 * a + 1]);",
+     lambda cav: TP.test_uniform_E_kick(cav, 1)),
+    ("gather: guide field B_z with the wrong sign",
+     "double Bf[3] = {0.0, Bavg[t] / area[t], bz};",
+     "double Bf[3] = {0.0, Bavg[t] / area[t], -bz};",
+     lambda cav: TP.test_boris_gyration_closed_form()),
+    ("walk: crossing parameter with the wrong sign",
+     "double s = l[k] / (l[k] - le[k]);",
+     "double s = l[k] / (le[k] - l[k]);",
+     lambda cav: TP.test_walk_reaches_the_straight_line_endpoint(cav)),
     ("Boris: s = 2t without the 1/(1 + t^2)",
      "sv[i] = 2.0 * tv[i] / (1.0 + t2);",
      "sv[i] = 2.0 * tv[i];",
