@@ -204,6 +204,9 @@ class Sim:
     def __init__(self, ptr, mesh):
         self.ptr = ptr
         self.mesh = mesh          # the mesh must outlive the simulation
+        # the library keeps the allocator hooks a simulation was created with and calls
+        # them when it frees its memory: keep their trampolines alive as long
+        self._hooks = _torch_hooks
         _live_sims.add(self)
 
     def __del__(self):
@@ -524,6 +527,7 @@ class Mlp:
         self.ptr = ptr
         self.members = members
         self.sizes = tuple(sizes)
+        self._hooks = _torch_hooks   # allocator trampolines the library keeps (see Sim)
 
     def __del__(self):
         if getattr(self, "ptr", None):

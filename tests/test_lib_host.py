@@ -194,3 +194,18 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
                          timeout=120, cwd=str(tmp_path))
     assert out.returncode == 0 and "refused: libpic_gb300.so is not built" in out.stdout, out
+
+
+def test_handles_keep_the_allocator_hooks_they_were_made_with(pic):
+    """The library calls a handle's allocator hooks again when the handle is freed, so the
+    binding keeps their ctypes trampolines alive with the handle, even after the process
+    installs other hooks."""
+    import gc
+    pic.pic_set_allocator(lambda n, ctx: None, lambda p, ctx: None)
+    hooks = pic._torch_hooks
+    s = pic.Sim(None, None)
+    n = pic.Mlp(None, 1, [1, 1])
+    pic.pic_set_allocator()
+    gc.collect()
+    assert pic._torch_hooks is None
+    assert s._hooks is hooks and n._hooks is hooks and hooks is not None
