@@ -216,6 +216,7 @@ class Sim:
 
 
 _live_sims = weakref.WeakSet()
+_live_mlps = weakref.WeakSet()
 
 
 @atexit.register
@@ -225,6 +226,10 @@ def _destroy_live_sims():
         if s.ptr:
             _lib.pic_sim_destroy(s.ptr)
             s.ptr = None
+    for n in list(_live_mlps):
+        if n.ptr:
+            _lib.pic_mlp_destroy(n.ptr)
+            n.ptr = None
 
 
 def pic_mesh_create(nodes_zr, tris, bedge_nodes, bedge_tag, eps0=1.0, mu0=1.0, c=None,
@@ -528,6 +533,7 @@ class Mlp:
         self.members = members
         self.sizes = tuple(sizes)
         self._hooks = _torch_hooks   # allocator trampolines the library keeps (see Sim)
+        _live_mlps.add(self)
 
     def __del__(self):
         if getattr(self, "ptr", None):

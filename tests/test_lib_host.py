@@ -209,3 +209,5 @@ def test_handles_keep_the_allocator_hooks_they_were_made_with(pic):
     gc.collect()
     assert pic._torch_hooks is None
     assert s._hooks is hooks and n._hooks is hooks and hooks is not None
+    # both kinds of handle are freed at exit, while the hooks' owner is still alive
+    assert s in pic._live_sims and n in pic._live_mlps
