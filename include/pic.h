@@ -185,6 +185,18 @@ pic_status pic_sim_set_sort_interval(pic_sim *s, int32_t interval);
 enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
 pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher);
 
+/* Bound of the particle kernel's tile-pipeline waits (FP32 build): the number of polls,
+ * each suspending the waiting thread for at most 100 us, that a wait for a staged tile
+ * (or for the release of a buffer) makes before it gives up.  Default 16384 (about 1.6 s).
+ * A wait that gives up is counted on the device; the block then stops, and before it
+ * exits it waits, with the default bound, for every copy into its shared memory still in
+ * flight, so a give-up never leaves a copy running.  Not an operation of the paper: it
+ * lets a caller (a test) make the waits run out, with 0 polls, and see the step reported
+ * as PIC_ERR_TIMEOUT by the next pic_diagnostics, pic_charges_get or
+ * pic_charges_get_static.  The simulation's state is invalid after that.
+ * Errors: ARG (null handle, negative count). */
+pic_status pic_sim_set_wait_limit(pic_sim *s, int64_t polls);
+
 /* Sources either side of the particle loop (Secs. 5.2, 5.3).
  *
  * The static (gun) field of the electrodes, by Poisson's equation (Sec. 5.3): the node
@@ -317,7 +329,7 @@ pic_status pic_particles_inject(pic_sim *s, int64_t n, const double *z, const do
  * Asynchronous: returns once the work is enqueued; the state stays on the device.
  * n_steps = 0 enqueues nothing.  A bounded device wait that gives up (a stalled copy
  * pipeline) is counted on the device and reported as PIC_ERR_TIMEOUT by the next
- * pic_diagnostics.  Errors: ARG (null handle, n_steps < 0), CUDA (a launch or graph
+ * pic_diagnostics, pic_charges_get or pic_charges_get_static.  Errors: ARG (null handle, n_steps < 0), CUDA (a launch or graph
  * call failed). */
 pic_status pic_step(pic_sim *s, int64_t n_steps, void *cuda_stream);
 
@@ -331,7 +343,8 @@ pic_status pic_diagnostics(pic_sim *s, pic_diag *out, double *E_out, double *B_o
                            double *J_out, void *cuda_stream);
 
 /* Node charges in physical units (N0 each, may be NULL): Q^n, Q^{n-1} and the charge
- * absorbed at walls during the last step. */
+ * absorbed at walls during the last step.  Synchronous.  Errors: ARG, OOM, CUDA, TIMEOUT
+ * (a bounded device wait of an earlier step gave up; nothing is written). */
 pic_status pic_charges_get(pic_sim *s, double *Q, double *Q_prev, double *Q_absorbed,
                            void *cuda_stream);
 
@@ -347,7 +360,8 @@ pic_status pic_charges_get(pic_sim *s, double *Q, double *Q_prev, double *Q_abso
  * before any stream capture.  Meshes with more than 131072 nodes are rejected with
  * PIC_ERR_ARG (use pic_charges_get).  All calls share the one array, so calls whose GPU
  * work overlaps (different streams or threads) race; each call synchronises its stream
- * before returning.  Q, Q_prev, Q_absorbed: N0 doubles each, or NULL. */
+ * before returning.  Q, Q_prev, Q_absorbed: N0 doubles each, or NULL.  TIMEOUT as for
+ * pic_charges_get (checked before anything is written). */
 pic_status pic_charges_get_static(pic_sim *s, double *Q, double *Q_prev, double *Q_absorbed,
                                   void *cuda_stream);
 
@@ -390,6 +404,12 @@ pic_status pic_step_host(pic_sim *s, void *host_state, int64_t n_slots, int64_t 
  * total milliseconds and the number of launches. */
 pic_status pic_kernel_timing(pic_sim *s, int32_t enable, double *push_ms, int64_t *launches,
                              void *cuda_stream);
+
+/* Number of kernels this library has enqueued for execution in the process so far, on
+ * any device and stream (launched directly, or as nodes of a replayed CUDA graph: a graph
+ * adds its kernels at each replay, its capture adds none).  Not an operation of the
+ * paper; a benchmark reads it before and after a timed region.  Errors: ARG (NULL out). */
+pic_status pic_launch_count(int64_t *out);
 
 /* ---- Surrogate network ensemble (not in the paper) ------------------------------------
  * An ensemble of n_members multilayer perceptrons with layer widths sizes[0..n_layers]

@@ -157,12 +157,15 @@ void launch_diag(const DiagDev &d, const typename P::Acc *J, const typename P::A
                  int64_t n_bound, double q_scale, double inv_c2, double *out, cudaStream_t s) {
     k_diag_nodes<P><<<(unsigned)((d.N0 + 255) / 256), 256, 0, s>>>(d, J, Qn, Qp, Qabs, Qpos, Qwall, D, dgl_ref,
                                                                    set_ref, q_scale, out);
+    PIC_LAUNCHED();
     if (set_ref) return;
     int64_t ne = d.N1 > d.N2 ? d.N1 : d.N2;
     k_diag_energy<P><<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(d, E, B, mu_inv, out);
+    PIC_LAUNCHED();
     if (n_bound > 0) {
         const int64_t blocks = std::min<int64_t>((n_bound + 255) / 256, 1216);
         k_diag_kinetic<P><<<(unsigned)blocks, 256, 0, s>>>(p, n_slots, inv_c2, out);
+        PIC_LAUNCHED();
     }
 }
 
@@ -195,6 +198,7 @@ void launch_export(Particles<P> p, int64_t n, const TriRec<typename P::R> *, dou
                    double *u3, int64_t *pid, cudaStream_t s) {
     if (n <= 0) return;
     k_export<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, lam3, u3, pid);
+    PIC_LAUNCHED();
 }
 
 template <class Acc>
@@ -210,6 +214,7 @@ void launch_acc_to_double(const typename P::Acc *a, double *out, int64_t n, doub
                           cudaStream_t s) {
     if (n <= 0) return;
     k_acc_to_double<typename P::Acc><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, out, n, scale);
+    PIC_LAUNCHED();
 }
 
 #define PIC_INST(P)                                                                            \

@@ -121,6 +121,7 @@ template <class P>
 void launch_emit(const EmitArgs<P> &a, cudaStream_t s) {
     if (a.per_step <= 0 || a.line.n <= 0) return;
     k_emit<P><<<1, EMIT_THREADS, 0, s>>>(a);
+    PIC_LAUNCHED();
 }
 
 template void launch_emit<PF32>(const EmitArgs<PF32> &, cudaStream_t);

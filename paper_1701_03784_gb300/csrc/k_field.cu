@@ -195,6 +195,7 @@ void launch_field_b(const FieldArgs<P> &a, cudaStream_t s) {
     else if (a.Es) k_field_b<P, true, false><<<g, b, 0, s>>>(a);
     else if (a.loss_f) k_field_b<P, false, true><<<g, b, 0, s>>>(a);
     else k_field_b<P, false, false><<<g, b, 0, s>>>(a);
+    PIC_LAUNCHED();
 }
 
 template <class P>
@@ -202,9 +203,11 @@ void launch_field_e(const FieldArgs<P> &a, cudaStream_t s) {
     const int64_t n = std::max(a.nf, a.N0);
     const int b = a.block;
     k_field_r<P><<<(unsigned)((n + b - 1) / b), b, 0, s>>>(a);
+    PIC_LAUNCHED();
     int64_t rows = ((a.nf + 31) / 32) * 32;
     if (a.loss_e) k_field_spmv<P, true><<<(unsigned)((rows + b - 1) / b), b, 0, s>>>(a);
     else k_field_spmv<P, false><<<(unsigned)((rows + b - 1) / b), b, 0, s>>>(a);
+    PIC_LAUNCHED();
 }
 
 template void launch_field_b<PF32>(const FieldArgs<PF32> &, cudaStream_t);

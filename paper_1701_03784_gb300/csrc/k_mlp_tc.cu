@@ -385,6 +385,7 @@ void mlp_tc_pack(const MlpTc &tc, const float *params, long long P, const long l
         pa.boff[l] = boff[l];
     }
     k_mlp_pack<<<dim3(64, tc.E * tc.L), 256, 0, s>>>(tc, params, P, pa);
+    PIC_LAUNCHED();
 }
 
 bool mlp_tc_gemm(const TcGemmOp &g, int E, uint16_t *scratch_a, uint16_t *scratch_b,
@@ -404,11 +405,14 @@ bool mlp_tc_gemm(const TcGemmOp &g, int E, uint16_t *scratch_a, uint16_t *scratc
     // A as an M x K matrix; B as the N x K matrix of its transpose (both K-major)
     k_tc_pack_op<<<dim3(64, E), 256, 0, s>>>(g.A, g.sAz, g.sAm, g.sAk, g.M, g.K, Mp, Kp,
                                              scratch_a, (long long)Mp * Kp);
+    PIC_LAUNCHED();
     k_tc_pack_op<<<dim3(64, E), 256, 0, s>>>(g.B, g.sBz, g.sBn, g.sBk, g.N, g.K, Np, Kp,
                                              scratch_b, (long long)Np * Kp);
+    PIC_LAUNCHED();
     const TcGemmDev d{scratch_a, scratch_b, (long long)Mp * Kp, (long long)Np * Kp, g.C, g.sCz,
                       g.ldc, g.M, g.N, Kp, Np, g.accumulate, err};
     k_tc_gemm<<<dim3((unsigned)(Mp / TM), (unsigned)E), TM, smem, s>>>(d);
+    PIC_LAUNCHED();
     return true;
 }
 
@@ -419,6 +423,7 @@ pic_status mlp_tc_forward(const MlpTc &tc, const float *X, float *Y, int64_t n, 
     PIC_CUDA_TRY(cudaMemsetAsync(tc.err, 0, sizeof(unsigned int), s));
     dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)tc.E);
     k_mlp_tc<<<grid, NTH, smem, s>>>(tc, X, Y, (long long)n);
+    PIC_LAUNCHED();
     PIC_CUDA_TRY(cudaGetLastError());
     unsigned int err = 0;
     PIC_CUDA_TRY(cudaMemcpyAsync(&err, tc.err, sizeof(err), cudaMemcpyDeviceToHost, s));

@@ -61,6 +61,7 @@ template <class P>
 void launch_probe(const ProbeArgs<P> &a, cudaStream_t s) {
     if (a.n_groups <= 0) return;
     k_probe<P><<<(unsigned)a.n_groups, 256, 0, s>>>(a);
+    PIC_LAUNCHED();
 }
 
 template void launch_probe<PF32>(const ProbeArgs<PF32> &, cudaStream_t);

@@ -409,6 +409,7 @@ void launch_push(const PushArgs<P> &a, int64_t n_bound, cudaStream_t s) {
         if (n_bound <= 0) return;
         int64_t blocks = (n_bound + 255) / 256;
         k_push<P><<<(unsigned)blocks, 256, 0, s>>>(a);
+        PIC_LAUNCHED();
     }
 }
 
@@ -446,6 +447,7 @@ void launch_deposit_q(const TriRec<typename P::R> *rec, Particles<P> p, int64_t 
                       int64_t count, typename P::Acc *Q, cudaStream_t s) {
     if (count <= 0) return;
     k_deposit_q<P><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(rec, p, first, count, Q);
+    PIC_LAUNCHED();
 }
 
 template void launch_push<PF32>(const PushArgs<PF32> &, int64_t, cudaStream_t);

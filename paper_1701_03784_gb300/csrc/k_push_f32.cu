@@ -24,8 +24,8 @@
 //    the segment to the first edge reached, its currents (direct atomics), then the
 //    neighbour (entered through a precomputed local edge index) until the end point,
 //    the axis, a wall or the walk cap.  The remainder (< 32) is walked at the end.
-// Every wait is bounded: on timeout the error counter is set and the CTA leaves after a
-// bounded wait for its own bulk copy in flight.  Small arrays are indexed statically
+// Every wait is bounded: on timeout the error counter is set and the CTA leaves once the
+// producer lane has waited (bounded) for every bulk copy it issued.  Small arrays are indexed statically
 // (nothing in local memory); fixed <-> float conversions use exact magic-number
 // arithmetic instead of the quarter-rate converters.
 #include <algorithm>
@@ -49,7 +49,7 @@ constexpr int TILE = PT * ROUNDS;  // slots per tile
 constexpr int STAGES = 2;          // tile buffers in flight
 constexpr int QCAP = 64;           // ring entries per compute warp (at most 31 + 32 used)
 constexpr unsigned WAIT_SLICE_NS = 100000;    // one bounded mbarrier poll sleeps <= 100 us
-constexpr long long WAIT_LIMIT = 1LL << 14;   // polls before a wait gives up (<= ~1.6 s)
+constexpr long long WAIT_LIMIT = PUSH_WAIT_POLLS;   // polls of a drain wait (<= ~1.6 s)
 
 // s in [0, 2^23): exactly (float)s * 2^-22
 __device__ __forceinline__ float fix2f(int s) {
@@ -221,9 +221,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
         : "=r"(ok) : "r"(smem_u32(b)), "r"(parity), "n"(WAIT_SLICE_NS) : "memory");
     return ok != 0;
 }
-// bounded wait for the phase of the given parity; false when the limit is reached
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
-    for (long long k = 0; k < WAIT_LIMIT; k++)
+// bounded wait for the phase of the given parity; false when `polls` polls did not see it
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity,
+                                          long long polls = WAIT_LIMIT) {
+    for (long long k = 0; k < polls; k++)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }
@@ -491,12 +492,19 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
             for (long long tile = tile0; tile < tile1; tile++, it++) {
                 const int stage = (int)(it % STAGES);
                 if (it >= STAGES &&
-                    !mbar_wait(&sm.empty[stage], (unsigned)((it / STAGES - 1) & 1))) {
+                    !mbar_wait(&sm.empty[stage], (unsigned)((it / STAGES - 1) & 1), a.wait_polls)) {
                     atomicAdd(a.counters + CNT_TIMEOUT, 1ULL);
                     break;
                 }
                 issue_tile(a, sm, stage, tile, n);
             }
+            // before the block can exit, every copy issued into its shared memory has
+            // landed: wait (bounded) for the last phase issued on each stage.  After a
+            // normal run the compute warps have seen these phases and the waits return at
+            // once; after a timeout they may not have.
+            for (long long k = it > STAGES ? it - STAGES : 0; k < it; k++)
+                if (!mbar_wait(&sm.full[(int)(k % STAGES)], (unsigned)((k / STAGES) & 1)))
+                    atomicAdd(a.counters + CNT_TIMEOUT, 1ULL);
         }
     } else {
         // ---- compute warps.  Particles that leave their start triangle go to the warp's
@@ -507,13 +515,10 @@ __global__ void __launch_bounds__(NT, 4) k_push_f32(PushArgs<PF32> a) {
         long long it = 0;
         for (long long tile = tile0; tile < tile1; tile++, it++) {
             const int stage = (int)(it % STAGES);
-            const bool ok = mbar_wait(&sm.full[stage], (unsigned)((it / STAGES) & 1));
+            const bool ok = mbar_wait(&sm.full[stage], (unsigned)((it / STAGES) & 1), a.wait_polls);
             if (__any_sync(full, !ok)) {
-                if (lane == 0) {
-                    // give the stage's bulk copies one more bounded wait before leaving
-                    atomicAdd(a.counters + CNT_TIMEOUT, 1ULL);
-                    mbar_wait(&sm.full[stage], (unsigned)((it / STAGES) & 1));
-                }
+                // leave; the producer drains the copies in flight before the block exits
+                if (lane == 0) atomicAdd(a.counters + CNT_TIMEOUT, 1ULL);
                 break;
             }
             const TileBuf &b = sm.buf[stage];
@@ -594,6 +599,7 @@ static void launch_push_f32_as(const PushArgs<PF32> &a, int64_t n_bound, cudaStr
     const int bps = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, ps.bps) : ps.bps;
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)ps.sms * bps);
     k_push_f32<VAY><<<(unsigned)grid, NT, smem, s>>>(a);
+    PIC_LAUNCHED();
 }
 
 void launch_push_f32(const PushArgs<PF32> &a, int64_t n_bound, cudaStream_t s) {

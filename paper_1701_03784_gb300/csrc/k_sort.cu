@@ -240,11 +240,16 @@ void launch_resort(Particles<P> src, Particles<P> dst, int64_t *n_slots, int64_t
     int64_t *n_old = sc.n_old;
     unsigned pb = (unsigned)std::max<int64_t>(1, (n_bound + SORT_CHUNK - 1) / SORT_CHUNK);
     k_count<P><<<pb, 256, 0, s>>>(src, n_slots, n_old, sc.cnt);
+    PIC_LAUNCHED();
     int64_t nblk = (N2 + SCAN_CHUNK - 1) / SCAN_CHUNK;
     k_scan_sums<<<(unsigned)nblk, 256, 0, s>>>(sc.cnt, N2, sc.blk);
+    PIC_LAUNCHED();
     k_scan_top<<<1, 256, 0, s>>>(sc.blk, nblk, n_slots);
+    PIC_LAUNCHED();
     k_scan_apply<<<(unsigned)nblk, 256, 0, s>>>(sc.cnt, N2, sc.blk);
+    PIC_LAUNCHED();
     k_scatter<P><<<pb, 256, 0, s>>>(src, dst, n_old, sc.cnt);
+    PIC_LAUNCHED();
 }
 
 template void launch_resort<PF32>(Particles<PF32>, Particles<PF32>, int64_t *, int64_t, int64_t,

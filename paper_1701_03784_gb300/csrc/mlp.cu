@@ -284,6 +284,7 @@ struct MlpImpl {
         }
         dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT, E);
         k_gemm<<<grid, dim3(GT, GT), 0, s>>>(g);
+        PIC_LAUNCHED();
     }
 
     // all layers for `rows` samples; the input of member z is X0 + z * sX0z (row-major)
@@ -298,6 +299,7 @@ struct MlpImpl {
             k_bias_act<<<dim3(blocks((long long)rows * N), E), 256, 0, s>>>(
                 pre[l], act[l + 1], params + boff[l], P, rows, N, (long long)max_batch * N,
                 l < L - 1);
+            PIC_LAUNCHED();
             A = act[l + 1];
             sAz = (long long)max_batch * N;
         }
@@ -311,16 +313,19 @@ struct MlpImpl {
         k_loss_grad<<<dim3(blocks((long long)rows * dout), E), 256, 0, s>>>(
             act[L], Tb, G, (long long)rows * dout, (long long)max_batch * dout,
             (long long)max_batch * dout, sg, 2.f / (float)((long long)rows * dout), loss_out);
+        PIC_LAUNCHED();
         // G is stored with the layer's width as row stride, member stride sg
         for (int l = L - 1; l >= 0; l--) {
             const int K = sz[l], N = sz[l + 1];
             if (l < L - 1)
                 k_gelu_back<<<dim3(blocks((long long)rows * N), E), 256, 0, s>>>(
                     G, pre[l], (long long)rows * N, sg, (long long)max_batch * N);
+                PIC_LAUNCHED();
             GemmArgs dw{G, act[l], grads + woff[l], N, K, rows, sg, (long long)max_batch * K, P,
                         1, N, K, 1, K, 0};
             gemm(dw, s);
             k_colsum<<<dim3(blocks(N), E), 256, 0, s>>>(G, grads + boff[l], rows, N, sg, P);
+            PIC_LAUNCHED();
             if (l > 0) {
                 GemmArgs dx{G, params + woff[l], Gn, rows, K, N, sg, P, sg, N, 1, K, 1, K, 0};
                 gemm(dx, s);
@@ -399,6 +404,7 @@ extern "C" pic_status pic_mlp_params_set(pic_mlp *m, const double *params) try {
     const long long n = x.E * x.P;
     PIC_CUDA_TRY(cudaMemcpy(x.stage, params, sizeof(double) * n, cudaMemcpyHostToDevice));
     k_to_f32<<<blocks(n), 256>>>(x.stage, x.params, n);
+    PIC_LAUNCHED();
     PIC_CUDA_TRY(cudaMemset(x.am, 0, sizeof(float) * n));
     PIC_CUDA_TRY(cudaMemset(x.av, 0, sizeof(float) * n));
     x.adam_step = 0;
@@ -435,6 +441,7 @@ extern "C" pic_status pic_mlp_grad(pic_mlp *m, const float *X, const float *T, i
     const int rows = (int)n;
     k_gather<<<dim3(blocks(rows), x.E), 256, 0, s>>>(X, T, x.act[0], x.Tb, n, rows, x.max_batch,
                                                      x.sz[0], x.sz[x.L], 0, 0, 0);
+    PIC_LAUNCHED();
     PIC_CUDA_TRY(cudaMemsetAsync(x.loss, 0, sizeof(float) * x.E, s));
     x.gemm_tc = x.train_tc;
     x.forward(rows, x.act[0], (long long)x.max_batch * x.sz[0], s);
@@ -471,6 +478,7 @@ extern "C" pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *T, 
         k_gather<<<dim3(blocks(batch), x.E), 256, 0, s>>>(X, T, x.act[0], x.Tb, n, batch,
                                                           x.max_batch, x.sz[0], x.sz[x.L], seed,
                                                           x.adam_step, 1);
+        PIC_LAUNCHED();
         const bool last = k == steps - 1;
         if (last) PIC_CUDA_TRY(cudaMemsetAsync(x.loss, 0, sizeof(float) * x.E, s));
         x.forward(batch, x.act[0], (long long)x.max_batch * x.sz[0], s);
@@ -481,6 +489,7 @@ extern "C" pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *T, 
         const float c2 = 1.f - std::pow(b2, (float)x.adam_step);
         k_adam<<<blocks(np), 256, 0, s>>>(x.params, x.grads, x.am, x.av, np, (float)lr, b1, b2,
                                           1e-8f, c1, c2);
+        PIC_LAUNCHED();
     }
     x.gemm_tc = false;
     PIC_CUDA_TRY(cudaGetLastError());
@@ -524,6 +533,7 @@ extern "C" pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int6
         x.forward(rows, X + c0 * din, 0, s);
         k_copy_out<<<dim3(blocks((long long)rows * dout), x.E), 256, 0, s>>>(
             x.act[x.L], Y, rows, dout, x.max_batch, n, c0);
+        PIC_LAUNCHED();
     }
     PIC_CUDA_TRY(cudaGetLastError());
     return PIC_OK;

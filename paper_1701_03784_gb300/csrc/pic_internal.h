@@ -177,6 +177,13 @@ bool build_emit_line(const HostMesh &m, double z0, double rho0, double rho1,
                      std::vector<double> &lam_a, std::vector<double> &lam_b,
                      std::vector<int32_t> &tri);
 
+// Kernels the library has enqueued for execution in this process.  Every launch site adds
+// one; a stream capture runs nothing, so the kernels it recorded are taken back out and
+// added again at each replay of the graph.
+void note_launches(long long k);
+long long launches_this_thread();
+#define PIC_LAUNCHED() ::pic::note_launches(1)
+
 // ---------------------------------------------------------------------------------
 // device layouts
 // ---------------------------------------------------------------------------------
@@ -254,7 +261,10 @@ struct PushArgs {
     int32_t walk_cap;
     int32_t ctas_per_sm;        // launch shape: persistent CTAs per SM (0: as many as fit)
     int32_t pusher;             // PIC_PUSHER_BORIS or PIC_PUSHER_VAY (Eq. DLE)
+    int64_t wait_polls;         // FP32 kernel: polls before a tile-pipeline wait gives up
 };
+// default of PushArgs::wait_polls (each poll suspends the thread for at most 100 us)
+constexpr int64_t PUSH_WAIT_POLLS = 1LL << 14;
 
 // Emission line z = const, cut into the triangles it crosses: interval k spans
 // rho in [rho_a[k], rho_b[k]] inside triangle tri[k], with barycentric coordinates lam_a

@@ -1,5 +1,6 @@
 // Simulation object: device-resident fields, operators and particles, and the per-step
 // launch sequence of the paper's cycle (Sec. 3).
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -8,6 +9,15 @@
 #include "pic_internal.h"
 
 namespace pic {
+
+static std::atomic<long long> g_launches{0};
+static thread_local long long t_launches = 0;
+
+void note_launches(long long k) {
+    g_launches += k;
+    t_launches += k;
+}
+long long launches_this_thread() { return t_launches; }
 
 static Allocator g_allocator;
 static std::mutex g_allocator_mu;
@@ -81,6 +91,7 @@ struct SimBase {
                                    cudaStream_t s) = 0;
     int32_t sort_interval = 16;
     int32_t pusher = PIC_PUSHER_BORIS;
+    int64_t wait_polls = PUSH_WAIT_POLLS;   // particle kernel's tile-pipeline waits
     int device = 0;
 };
 
@@ -148,7 +159,8 @@ struct SimImpl final : SimBase {
     cudaGraphExec_t g_exec = nullptr;
     int g_cur = 0, g_qcur = 0, g_since = 0, g_interval = -1, g_ctas = -1, g_block = -1, g_pusher = -1,
         g_src = -1;
-    int64_t g_bound = -1;
+    int64_t g_bound = -1, g_wait = -1;
+    long long g_kernels = 0;   // kernels recorded in g_exec
     cudaStream_t rt_stream = nullptr, up_stream = nullptr;
     cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr, rt_up = nullptr;
     std::vector<cudaEvent_t> ev_free;
@@ -765,7 +777,8 @@ struct SimImpl final : SimBase {
             }
             // a graph records the launch shapes and the pusher with the buffers
             if (g_exec && (g_bound != n_bound || g_interval != sort_interval || g_ctas != tune_ctas ||
-                           g_block != tune_block || g_pusher != pusher || g_src != src_version)) {
+                           g_block != tune_block || g_pusher != pusher || g_src != src_version ||
+                           g_wait != wait_polls)) {
                 cudaGraphExecDestroy(g_exec);
                 g_exec = nullptr;
             }
@@ -777,6 +790,7 @@ struct SimImpl final : SimBase {
             }
             if (!g_exec && (st = capture(L)) != PIC_OK) return st;
             PIC_CUDA_TRY(cudaGraphLaunch(g_exec, s));
+            note_launches(g_kernels);
             n_steps += L;
             done += L;
         }
@@ -856,12 +870,16 @@ struct SimImpl final : SimBase {
         g_ctas = tune_ctas;
         g_block = tune_block;
         g_pusher = pusher;
+        g_wait = wait_polls;
         g_src = src_version;
         PIC_CUDA_TRY(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
+        const long long k0 = launches_this_thread();
         pic_status st = step_direct(L, g_stream);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(g_stream, &graph);
         n_steps = n0;
+        g_kernels = launches_this_thread() - k0;   // recorded, not run
+        note_launches(-g_kernels);
         if (st != PIC_OK) {
             if (graph) cudaGraphDestroy(graph);
             return st;
@@ -931,6 +949,7 @@ struct SimImpl final : SimBase {
             pa.walk_cap = m->units.walk_cap;
             pa.ctas_per_sm = tune_ctas;
             pa.pusher = pusher;
+            pa.wait_polls = wait_polls;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (timing_on) {
                 e0 = take_event();
@@ -1064,6 +1083,19 @@ struct SimImpl final : SimBase {
         else cudaFree(p);
     }
 
+    // PIC_ERR_TIMEOUT if a bounded device wait of an earlier step gave up (the state is
+    // then invalid); synchronises the stream, allocates nothing
+    pic_status waits_ok(const char *who, cudaStream_t s) {
+        unsigned long long n = 0;
+        PIC_CUDA_TRY(cudaMemcpyAsync(&n, counters + CNT_TIMEOUT, sizeof n, cudaMemcpyDeviceToHost, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (n) {
+            set_error("%s: %llu bounded device waits timed out; the state is invalid", who, n);
+            return PIC_ERR_TIMEOUT;
+        }
+        return PIC_OK;
+    }
+
     // pic_charges_get without any allocation: the conversion kernel writes into the
     // library's static scratch, then each part is copied straight into the caller's
     // host array.  Every value of the used part is overwritten, so no clearing is needed.
@@ -1074,8 +1106,10 @@ struct SimImpl final : SimBase {
                       (long long)m->N0, (long long)STATIC_MAX_NODES);
             return PIC_ERR_ARG;
         }
+        pic_status st = waits_ok("pic_charges_get_static", s);
+        if (st != PIC_OK) return st;
         double *scr = nullptr;
-        pic_status st = charge_scratch_address(&scr);
+        st = charge_scratch_address(&scr);
         if (st != PIC_OK) return st;
         const double sc_ = (P::fixed ? LAM_INV : 1.0) * q_src;
         double *outs[3] = {Qo, Qpo, Qao};
@@ -1092,8 +1126,10 @@ struct SimImpl final : SimBase {
     }
 
     pic_status charges(double *Qo, double *Qpo, double *Qao, cudaStream_t s) override {
+        pic_status st = waits_ok("pic_charges_get", s);
+        if (st != PIC_OK) return st;
         double *tmp = nullptr;
-        pic_status st = dalloc(tmp, 3 * m->N0);
+        st = dalloc(tmp, 3 * m->N0);
         if (st != PIC_OK) return st;
         double sc_ = (P::fixed ? LAM_INV : 1.0) * q_src;
         launch_acc_to_double<P>(Qn(), tmp, m->N0, sc_, s);
@@ -1386,6 +1422,27 @@ extern "C" pic_status pic_sim_set_pusher(pic_sim *s, int32_t pusher) try {
     return PIC_OK;
 }
 PIC_CATCH("pic_sim_set_pusher")
+
+extern "C" pic_status pic_launch_count(int64_t *out) try {
+    if (!out) {
+        set_error("pic_launch_count: null output");
+        return PIC_ERR_ARG;
+    }
+    *out = (int64_t)g_launches.load();
+    return PIC_OK;
+}
+PIC_CATCH("pic_launch_count")
+
+extern "C" pic_status pic_sim_set_wait_limit(pic_sim *s, int64_t polls) try {
+    SIM_CHECK(s, "pic_sim_set_wait_limit");
+    if (polls < 0) {
+        set_error("pic_sim_set_wait_limit: negative poll count");
+        return PIC_ERR_ARG;
+    }
+    s->impl->wait_polls = polls;
+    return PIC_OK;
+}
+PIC_CATCH("pic_sim_set_wait_limit")
 
 extern "C" pic_status pic_sim_set_static_field(pic_sim *s, const double *E_static, void *st) try {
     SIM_CHECK(s, "pic_sim_set_static_field");

@@ -73,6 +73,7 @@ _SIGS = {
     "pic_sim_create": [_P, _D, _D, _I64, _P],
     "pic_sim_set_sort_interval": [_P, _I32],
     "pic_sim_set_pusher": [_P, _I32],
+    "pic_sim_set_wait_limit": [_P, _I64],
     "pic_static_potential": [_P, _I64, _P, _P, _P, _P, _P],
     "pic_sim_set_static_field": [_P, _P, _P],
     "pic_sim_set_emitter": [_P, ctypes.POINTER(pic_emitter), _P],
@@ -102,6 +103,7 @@ _SIGS = {
     "pic_particles_raw_set": [_P, _P, _I64, _P],
     "pic_step_host": [_P, _P, _I64, _I64, _P],
     "pic_kernel_timing": [_P, _I32, _P, _P, _P],
+    "pic_launch_count": [_P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -378,6 +380,11 @@ def pic_sim_set_pusher(sim, pusher):
     _check(_lib.pic_sim_set_pusher(sim.ptr, pusher), "pic_sim_set_pusher")
 
 
+def pic_sim_set_wait_limit(sim, polls):
+    """Polls before a tile-pipeline wait of the particle kernel gives up (default 16384)."""
+    _check(_lib.pic_sim_set_wait_limit(sim.ptr, int(polls)), "pic_sim_set_wait_limit")
+
+
 def pic_sim_set_graph(sim, enable=True):
     _check(_lib.pic_sim_set_graph(sim.ptr, 1 if enable else 0), "pic_sim_set_graph")
 
@@ -446,8 +453,21 @@ def pic_charges_get_static(sim, Q=None, Q_prev=None, Q_absorbed=None, stream=Non
     """pic_charges_get for callers that must not allocate device memory (the library's
     fixed scratch is used instead; meshes up to 131072 nodes).  The output arrays are the
     caller's (float64, N0 each) and are filled in place; None skips one."""
-    for x in (Q, Q_prev, Q_absorbed):
-        assert x is None or (x.dtype == np.float64 and x.flags.c_contiguous)
+    n0 = pic_mesh_info(sim.mesh)["n_nodes"]
+    for name, x in (("Q", Q), ("Q_prev", Q_prev), ("Q_absorbed", Q_absorbed)):
+        # the library writes N0 doubles through each non-NULL pointer: anything that is not
+        # a writeable, C-contiguous float64 array of exactly N0 elements is refused here,
+        # before the call
+        if x is None:
+            continue
+        if not isinstance(x, np.ndarray):
+            raise ValueError("pic_charges_get_static: %s must be a numpy array" % name)
+        if x.dtype != np.float64 or not x.flags.c_contiguous or not x.flags.writeable:
+            raise ValueError("pic_charges_get_static: %s must be a writeable, C-contiguous "
+                             "float64 array" % name)
+        if x.size != n0:
+            raise ValueError("pic_charges_get_static: %s has %d elements, the mesh has %d "
+                             "nodes" % (name, x.size, n0))
     _check(_lib.pic_charges_get_static(sim.ptr, _ptr(Q), _ptr(Q_prev), _ptr(Q_absorbed),
                                        _stream(stream)), "pic_charges_get_static")
     return Q, Q_prev, Q_absorbed
@@ -511,6 +531,14 @@ def pic_kernel_timing(sim, enable=True, stream=None):
     _check(_lib.pic_kernel_timing(sim.ptr, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(n),
                                   _stream(stream)), "pic_kernel_timing")
     return ms.value, n.value
+
+
+def pic_launch_count():
+    """Kernels the library has enqueued for execution in this process (graph replays
+    count their kernels)."""
+    n = ctypes.c_int64()
+    _check(_lib.pic_launch_count(ctypes.byref(n)), "pic_launch_count")
+    return n.value
 
 
 def pic_sim_destroy(sim):

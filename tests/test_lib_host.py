@@ -211,3 +211,24 @@ def test_handles_keep_the_allocator_hooks_they_were_made_with(pic):
     assert s._hooks is hooks and n._hooks is hooks and hooks is not None
     # both kinds of handle are freed at exit, while the hooks' owner is still alive
     assert s in pic._live_sims and n in pic._live_mlps
+
+
+def test_static_charge_outputs_are_checked_before_the_call(pic):
+    """pic_charges_get_static writes N0 doubles through each output it is given: a short,
+    read-only, non-contiguous or non-float64 array is refused in the binding, before the
+    library is called (a handle with a NULL simulation pointer would fail there)."""
+    nodes, tris, be, bt = W.two_triangle_mesh()
+    mesh = pic.pic_mesh_create(nodes, tris, be, bt)
+    n0 = pic.pic_mesh_info(mesh)["n_nodes"]
+    sim = pic.Sim.__new__(pic.Sim)
+    sim.ptr, sim.mesh = None, mesh
+    ro = np.zeros(n0)
+    ro.flags.writeable = False
+    bad = [np.zeros(n0 - 1), np.zeros(n0 + 1), np.zeros(n0, np.float32), ro,
+           np.zeros(2 * n0)[::2], list(np.zeros(n0))]
+    for x in bad:
+        for pos in range(3):
+            args = [None, None, None]
+            args[pos] = x
+            with pytest.raises(ValueError):
+                pic.pic_charges_get_static(sim, *args)
