@@ -25,3 +25,4 @@ from .particles import (  # noqa: E402
     uniform_in_volume_rect, bwo_beam, uniform_in_mesh, maxwellian, cavity_particles,
 )
 from .fields import tm0np_edge_dofs, tm0np_omega, random_edge_values  # noqa: E402
+from .cavity import cavity_workload, cavity_weight, cavity_modes  # noqa: E402
