@@ -90,6 +90,76 @@ def clock_summary(p, rows):
             "samples": len(sm)}
 
 
+class NvmlClocks:
+    """SM clock and clock-event (throttle) reasons of this process's GPU, read through NVML
+    (libnvidia-ml, read-only queries) once before the timed region, every 2 ms by a thread
+    while it runs, and once after it: a region of a few milliseconds still gets samples."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device=0):
+        import ctypes
+        self.ok = False
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            self.lib, self.ct = lib, ctypes
+            h = ctypes.c_void_p()
+            bus = None
+            try:
+                import torch
+                pr = torch.cuda.get_device_properties(torch_device)
+                bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            except Exception:
+                bus = None
+            if bus is None or lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+                if lib.nvmlDeviceGetHandleByIndex_v2(int(os.environ.get("LOCAL_RANK", "0")),
+                                                     ctypes.byref(h)) != 0:
+                    return
+            self.h = h
+            mx = ctypes.c_uint()
+            lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))   # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+            self.ok = True
+        except (OSError, AttributeError):
+            self.ok = False
+
+    def read(self):
+        c = self.ct.c_uint()
+        r = self.ct.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(c))
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(self.h, self.ct.byref(r))
+        return float(c.value), int(r.value)
+
+    def start(self):
+        self.samples = [self.read()] if self.ok else []
+        self._stop = threading.Event()
+        if self.ok:
+            def poll():
+                while not self._stop.wait(0.002):
+                    self.samples.append(self.read())
+            self._t = threading.Thread(target=poll, daemon=True)
+            self._t.start()
+
+    def stop(self):
+        if not self.ok:
+            return None
+        self._stop.set()
+        self._t.join()
+        self.samples.append(self.read())
+        reasons = set()
+        for _, bits in self.samples:
+            for b, name in self.REASONS.items():
+                if bits & b:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples),
+                "sm_mhz_min": min(m for m, _ in self.samples), "source": "nvml"}
+
+
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
@@ -124,7 +194,7 @@ class OracleSample:
     a bounded sample of the same workload: the same mesh, fields and step, the first
     n_sample beam particles."""
 
-    def __init__(self, wl, n_sample=CPU_SAMPLE, pusher="boris"):
+    def __init__(self, wl, n_sample=CPU_SAMPLE, pusher="boris", threads=False):
         from oracle.operators import Mesh
         from oracle import particles as OP
         import workloads as W
@@ -145,6 +215,7 @@ class OracleSample:
         self.n_edges = m.N1
         self.q_src = wl["weight"] * QE / (2 * math.pi)
         self.pusher = OP.VAY if pusher == "vay" else OP.BORIS
+        self.threads = threads
 
     def step(self):
         """One particle step of the sample; returns (wall time in seconds, particles
@@ -155,23 +226,45 @@ class OracleSample:
         self.Q[:] = 0
         self.OP.push(self.pm, self.E, self.Bavg, self.wl["bz"], self.wl["dt"], QE / ME, C0,
                      self.q_src, self.tri, self.lam, self.u, self.J, self.Q, self.Qa,
-                     pusher=self.pusher)
+                     pusher=self.pusher, threads=self.threads)
         return time.perf_counter() - t0, live
 
 
-def cpu_baseline(wl, budget_s=15.0, pusher="boris"):
-    s = OracleSample(wl, pusher=pusher)
+CPU_SAMPLE_THREADS = 1_600_000   # the OpenMP run's sample: enough particles per thread
+
+
+def _time_sample(s, budget_s):
     done, el, pushed = 0, 0.0, 0
     while el < budget_s:
         dt_s, n = s.step()
         el += dt_s
         pushed += n
         done += 1
-    live = int(np.count_nonzero(s.tri >= 0))
-    return {"value": pushed / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of %d beam particles, %d steps, same mesh, fields and dt; FP64 C "
-                      "oracle particle loop (gather, %s, walk, scatter), single thread; %d "
-                      "live at end" % (s.n, len(wl["z"]), done, pusher.capitalize(), live)}
+    return pushed / el, done
+
+
+def cpu_baseline(wl, budget_s=8.0, pusher="boris"):
+    """The oracle's particle loop on the host: the same particles.c built with OpenMP (all
+    host cores, atomic accumulators) on a 1.6M-particle sample, and the plain
+    single-threaded build on a 160k sample, each for about budget_s seconds."""
+    from oracle import particles as OP
+    single, n1 = _time_sample(OracleSample(wl, CPU_SAMPLE, pusher), budget_s)
+    out = {"unit": "particle-steps/s", "kind": "oracle", "single_thread": single}
+    try:
+        threads = OP.host_threads(True)
+        s = OracleSample(wl, CPU_SAMPLE_THREADS, pusher, threads=True)
+        multi, nm = _time_sample(s, budget_s)
+        out.update(value=multi, cores=threads, sample=(
+            "FP64 C oracle particle loop (gather, %s, walk, scatter), same mesh, fields and dt: "
+            "OpenMP build on %d host threads (nproc %d), the first %d of %d beam particles, "
+            "%d steps; single-thread build (single_thread) on the first %d, %d steps"
+            % (pusher.capitalize(), threads, os.cpu_count() or 0, CPU_SAMPLE_THREADS,
+               len(wl["z"]), nm, CPU_SAMPLE, n1)))
+    except RuntimeError:
+        out.update(value=single, cores=1, sample=(
+            "FP64 C oracle particle loop, single thread (no OpenMP compiler), the first %d of "
+            "%d beam particles, %d steps" % (CPU_SAMPLE, len(wl["z"]), n1)))
+    return out
 
 
 def reduce_over_ranks(ms, e2e_ms, n_particles, n_slots, dist=None, device="cpu"):
@@ -186,23 +279,34 @@ def reduce_over_ranks(ms, e2e_ms, n_particles, n_slots, dist=None, device="cpu")
     return t.tolist(), c.tolist()
 
 
-def run_config(args, n_tris, n_edges, dt):
-    """The workload named in both arms' JSON lines."""
+def run_config(args, n_tris, n_edges, dt, sort_interval=None):
+    """The workload named in both arms' JSON lines (sort_interval: the one in force during
+    the timed steps, after the autotuner)."""
     return {"workload": "single BWO (rippled SWS, 12 periods), %d triangles, %d particles, "
                         "FP32 + int64 fixed-point J/Q" % (n_tris, args.particles),
             "n_tris": n_tris, "n_edges": n_edges, "particles": args.particles, "dt_s": dt,
-            "sort_interval": args.sort_interval, "pusher": args.pusher,
+            "sort_interval": args.sort_interval if sort_interval is None else sort_interval,
+            "pusher": args.pusher,
             "l2": "inputs larger than L2 (particle state %d MB)" % (args.particles * 24 // 2 ** 20),
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle's particle loop (the OpenMP build, on all host
+    cores; the plain build if the compiler has no OpenMP), each step a bounded sample of
+    the workload (its first 1.6M beam particles), rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import particles as OP
     wl = workload(args.particles)
     wl["dt"] = args.dt or DT_BWO
-    s = OracleSample(wl, pusher=args.pusher)
+    try:
+        cores = OP.host_threads(True)
+        s = OracleSample(wl, CPU_SAMPLE_THREADS, pusher=args.pusher, threads=True)
+    except RuntimeError:
+        cores = 1
+        s = OracleSample(wl, CPU_SAMPLE, pusher=args.pusher)
     t, pushed = 0.0, 0
     for i in range(args.warmup + args.steps):
         el, n = s.step()
@@ -210,9 +314,10 @@ def run_reference(args):
             t += el
             pushed += n
     value = pushed / t
-    cb = {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-          "sample": "%d of %d particles per step (bounded sample of the workload), FP64 C "
-                    "oracle particle loop, single thread" % (CPU_SAMPLE, args.particles)}
+    cb = {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+          "sample": "the first %d of %d particles per step (bounded sample of the workload), "
+                    "FP64 C oracle particle loop on %d host threads (nproc %d)"
+                    % (s.n, args.particles, cores, os.cpu_count() or 0)}
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -228,28 +333,22 @@ def run_reference(args):
 SWEEP_RUN_STEPS = 100_000   # one run of an instance: the single-BWO configuration's length
 
 
-def run_sweep(args):
-    """Batched ripple sweep: the union of N seeded BWO instances advanced as one
-    simulation (one particle-kernel launch per step over every instance) against the same
-    N instances run one after another, each as its own simulation, over the same steps and
-    time step.  Runs per hour are for runs of SWEEP_RUN_STEPS steps."""
+def sweep_measure(n_inst, steps, warmup, sort_interval=16, tune=True, graph=True, rank=0,
+                  world=1, dist=None):
+    """Batched ripple sweep: the union of n_inst seeded BWO instances (seeds 0..n_inst-1)
+    advanced as one simulation (one particle-kernel launch per step over every instance)
+    against the same instances run one after another, each as its own simulation, over
+    the same steps and time step (0.5 x the union's stable step, i.e. the smallest
+    instance limit).  Across ranks the instances are sharded (one union per rank, nothing
+    exchanged) and the job's time is the slowest rank's.  Runs per hour are for runs of
+    SWEEP_RUN_STEPS steps."""
     import torch
-    import paper_1701_03784_gb300 as pkg
-    pkg.build()
     from paper_1701_03784_gb300 import pic
     from paper_1701_03784_gb300.batch import partition
     from workloads.sweep import sweep_instance, sweep_params, sweep_particles, union, WEIGHT
     from workloads.bwo import BZ_BWO
-    # across GPUs the instances are sharded (one union per rank, nothing exchanged)
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     t_setup = time.time()
-    work = [sweep_particles(i) + sweep_params(i)["n_tri"] for i in range(args.sweep)]
+    work = [sweep_particles(i) + sweep_params(i)["n_tri"] for i in range(n_inst)]
     mine = partition(work, world)[rank]
     ins = [sweep_instance(i) for i in mine]
     u = union(ins)
@@ -262,21 +361,22 @@ def run_sweep(args):
     mesh_u, dt_u = make(u)
     dt = 0.5 * dt_u
     stream = torch.cuda.current_stream()
+    tuned = []
 
     def timed(mesh, x):
         info = pic.pic_mesh_info(mesh)
         sim = pic.pic_sim_create(mesh, dt, BZ_BWO, len(x["z"]) + 1024)
-        pic.pic_sim_set_sort_interval(sim, args.sort_interval)
-        pic.pic_sim_set_graph(sim, not args.no_graph)
+        pic.pic_sim_set_sort_interval(sim, sort_interval)
+        pic.pic_sim_set_graph(sim, graph)
         pic.pic_fields_set(sim, np.zeros(info["n_edges"]), np.zeros(info["n_tris"]))
         pic.pic_particles_inject(sim, x["z"], x["r"], x["ur"], x["up"], x["uz"], QE, ME, WEIGHT)
-        tuned.append(None if args.no_tune else pic.pic_sim_autotune(sim, 16))
-        pic.pic_step(sim, args.sweep_warmup)
+        tuned.append(pic.pic_sim_autotune(sim, 16) if tune else None)
+        pic.pic_step(sim, warmup)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        pic.pic_step(sim, args.sweep_steps)
+        pic.pic_step(sim, steps)
         e1.record(stream)
         torch.cuda.synchronize()
         d = pic.pic_diagnostics(sim)
@@ -284,7 +384,6 @@ def run_sweep(args):
         return e0.elapsed_time(e1), d
 
     setup_s = time.time() - t_setup
-    tuned = []
     ms_b, d_b = timed(mesh_u, u)
     ms_p = 0.0
     for x in ins:
@@ -292,36 +391,56 @@ def run_sweep(args):
         ms, _ = timed(mesh, x)
         ms_p += ms
         del mesh
-    k = args.sweep_steps
-    # the job: the slowest rank's times, every rank's particles
     (ms_b, ms_p), (n_part, n_tris) = reduce_over_ranks(ms_b, ms_p, len(u["z"]), len(u["tris"]),
                                                         dist, device="cuda")
-    step_b, step_p = ms_b / k, ms_p / k
-    runs_b = args.sweep * 3600.0 / (SWEEP_RUN_STEPS * step_b * 1e-3)
-    runs_p = args.sweep * 3600.0 / (SWEEP_RUN_STEPS * step_p * 1e-3)
+    step_b, step_p = ms_b / steps, ms_p / steps
+    runs_b = n_inst * 3600.0 / (SWEEP_RUN_STEPS * step_b * 1e-3)
+    runs_p = n_inst * 3600.0 / (SWEEP_RUN_STEPS * step_p * 1e-3)
+    return {"runs_per_hour": {"batched": runs_b, "plain": runs_p}, "speedup": runs_b / runs_p,
+            "instances": n_inst, "seeds": "0..%d" % (n_inst - 1), "triangles": int(n_tris),
+            "particles": int(n_part), "dt_s": dt,
+            "dt_rule": "common step: 0.5 x the union's SPAI-stable step (the smallest instance "
+                       "limit), the same in both modes",
+            "timed_steps": steps, "warmup": warmup, "run_steps": SWEEP_RUN_STEPS,
+            "runs_per_hour_rule": "instances x 3600 s / (run_steps x timed ms per step)",
+            "cuda_graph": graph, "tuned_batched": tuned[0], "sort_interval_requested": sort_interval,
+            "ms_per_step": {"batched": step_b, "plain_sum": step_p},
+            "particle_steps_per_s": {"batched": n_part / (step_b * 1e-3),
+                                     "plain": n_part / (step_p * 1e-3)},
+            "checks": {"dce_nonzero_nodes": d_b["dce_nonzero"],
+                       "walk_overflows": d_b["walk_overflows"],
+                       "live_particles": d_b["n_particles"]},
+            "setup_s": setup_s}
+
+
+def run_sweep(args):
+    """--sweep N: the batched-sweep measurement alone, as its own JSON line."""
+    import torch
+    import paper_1701_03784_gb300 as pkg
+    pkg.build()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    r = sweep_measure(args.sweep, args.sweep_steps, args.sweep_warmup, args.sort_interval,
+                      not args.no_tune, not args.no_graph, rank, world, dist)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
         return 0
     print(json.dumps({
-        "metric": "batched runs/h vs plain", "value": runs_b, "unit": "runs/h",
-        "higher_is_better": True, "plain": runs_p, "speedup": runs_b / runs_p,
-        "n_gpus": world, "scaling": "strong", "steps": k, "warmup": args.sweep_warmup,
+        "metric": "batched runs/h vs plain", "value": r["runs_per_hour"]["batched"], "unit": "runs/h",
+        "higher_is_better": True, "plain": r["runs_per_hour"]["plain"], "speedup": r["speedup"],
+        "n_gpus": world, "scaling": "strong", "steps": args.sweep_steps, "warmup": args.sweep_warmup,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batched ripple sweep, %d BWO instances (seeds 0..%d)"
-                               % (args.sweep, args.sweep - 1),
-                   "instances": args.sweep, "triangles": int(n_tris),
-                   "parallelism": "instances sharded over %d GPUs" % world if world > 1 else "single",
-                   "particles": int(n_part), "dt_s": dt, "sort_interval": args.sort_interval,
-                   "run_steps": SWEEP_RUN_STEPS, "cuda_graph": not args.no_graph,
-                   "tuned_batched": tuned[0]},
-        "ms_per_step": {"batched": step_b, "plain_sum": step_p},
-        "particle_steps_per_s": {"batched": n_part / (step_b * 1e-3),
-                                 "plain": n_part / (step_p * 1e-3)},
-        "checks": {"dce_nonzero_nodes": d_b["dce_nonzero"], "walk_overflows": d_b["walk_overflows"],
-                   "live_particles": d_b["n_particles"]},
-        "setup_s": setup_s}))
+        "config": {"workload": "batched ripple sweep, %d BWO instances (seeds %s)"
+                               % (args.sweep, r["seeds"]),
+                   "parallelism": "instances sharded over %d GPUs" % world if world > 1 else "single"},
+        "batched": r}))
     return 0
 
 
@@ -625,6 +744,79 @@ def run_diode(args):
     return 0
 
 
+def _timed_steps(pic, sim, steps):
+    """(ms per step, ms per particle-kernel launch) over `steps` steps, CUDA events."""
+    import torch
+    torch.cuda.synchronize()
+    pic.pic_kernel_timing(sim, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pic.pic_step(sim, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    push_ms, n = pic.pic_kernel_timing(sim, False)
+    return e0.elapsed_time(e1) / steps, push_ms / max(n, 1)
+
+
+def measure_m3u(pic, mesh, wl, dt, peak, per_tri=100, steps=200, warmup=20):
+    """The same mesh with about per_tri particles per triangle spread uniformly (in area)
+    over the whole domain, momenta of the beam (400 kV drift along z, thermal 1e-3 u_z):
+    the contention-free counterpart of the beam workload.  FP32 build."""
+    import workloads as W
+    n_tris = len(wl["tris"])
+    n = per_tri * n_tris
+    uz0 = float(np.median(wl["uz"]))
+    z, r, ur, up, uz = W.uniform_in_mesh(wl["nodes"], wl["tris"], n, 2013, sigma_u=1e-3 * uz0,
+                                         drift=(0.0, 0.0, uz0))
+    info = pic.pic_mesh_info(mesh)
+    sim = pic.pic_sim_create(mesh, dt, wl["bz"], n + 1024)
+    pic.pic_fields_set(sim, bwo_edge_field(info["n_edges"], wl["e_scale"], 7), np.zeros(n_tris))
+    pic.pic_particles_inject(sim, z, r, ur, up, uz, QE, ME, wl["weight"])
+    pic.pic_step(sim, warmup)
+    live0 = pic.pic_diagnostics(sim)["n_particles"]
+    step_ms, push_ms = _timed_steps(pic, sim, steps)
+    live1 = pic.pic_diagnostics(sim)["n_particles"]
+    pic.pic_sim_destroy(sim)
+    avg = 0.5 * (live0 + live1)
+    gbs = BYTES_PER_PARTICLE * avg / (push_ms * 1e-3) / 1e9
+    return {"workload": "same mesh, %d particles uniform over all %d triangles (%d per "
+                        "triangle), beam momenta, FP32" % (n, n_tris, per_tri),
+            "value": avg / (step_ms * 1e-3), "unit": "particle-steps/s", "steps": steps,
+            "warmup": warmup, "ms_per_step": step_ms, "push_ms": push_ms,
+            "push_gbs": gbs, "push_frac_of_hbm": gbs / peak, "live_particles": [live0, live1]}
+
+
+BYTES_PER_PARTICLE_FP64 = 88   # FP64 build: 44 B of state read + 44 B written
+
+
+def measure_fp64(pic, wl, dt, peak, steps=200, warmup=20):
+    """The beam workload in the FP64 build (the paper's arithmetic): FP64 fields, particle
+    state and currents, the same mesh, particles and step."""
+    mesh = pic.pic_mesh_create(wl["nodes"], wl["tris"], wl["be"], wl["bt"], eps0=EPS0, mu0=MU0,
+                               c=C0, precision=pic.PIC_FP64)
+    pic.pic_spai_build(mesh, 2, 1e-4)
+    info = pic.pic_mesh_info(mesh)
+    n = len(wl["z"])
+    sim = pic.pic_sim_create(mesh, dt, wl["bz"], n + 1024)
+    pic.pic_fields_set(sim, bwo_edge_field(info["n_edges"], wl["e_scale"], 7),
+                       np.zeros(info["n_tris"]))
+    pic.pic_particles_inject(sim, wl["z"], wl["r"], wl["ur"], wl["up"], wl["uz"], QE, ME,
+                             wl["weight"])
+    pic.pic_step(sim, warmup)
+    live0 = pic.pic_diagnostics(sim)["n_particles"]
+    step_ms, push_ms = _timed_steps(pic, sim, steps)
+    d = pic.pic_diagnostics(sim)
+    pic.pic_sim_destroy(sim)
+    pic.pic_mesh_destroy(mesh)
+    avg = 0.5 * (live0 + d["n_particles"])
+    gbs = BYTES_PER_PARTICLE_FP64 * avg / (push_ms * 1e-3) / 1e9
+    return {"workload": "single BWO, %d particles, FP64 build" % n, "dtype": "f64",
+            "value": avg / (step_ms * 1e-3), "unit": "particle-steps/s", "steps": steps,
+            "warmup": warmup, "ms_per_step": step_ms, "push_ms": push_ms,
+            "bytes_per_particle": BYTES_PER_PARTICLE_FP64, "push_gbs": gbs,
+            "push_frac_of_hbm": gbs / peak, "dce_max": d["dce_max"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -638,6 +830,10 @@ def main():
                     help="velocity update of Eq. DLE (both arms)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra records (uniform-fill M3u, FP64 build, batched sweep)")
+    ap.add_argument("--batched", type=int, default=16,
+                    help="instances of the batched-sweep record in the default line (0: none)")
     ap.add_argument("--sweep", type=int, default=0,
                     help="batched ripple sweep over this many instances instead")
     ap.add_argument("--sweep-steps", type=int, default=64)
@@ -713,11 +909,21 @@ def main():
     tuned = None if args.no_tune else pic.pic_sim_autotune(sim, 32)
     pic.pic_step(sim, args.warmup)
     barrier()
-    n_live = pic.pic_diagnostics(sim)["n_particles"]
+    d0 = pic.pic_diagnostics(sim)
+    n_live = d0["n_particles"]
+    si = int(d0["sort_interval"])
+    # phase of the re-sort: the first timed step ends with one, so the K timed steps hold
+    # ceil(K / interval) re-sorts (never fewer than their amortised share)
+    if si > 0:
+        pic.pic_step(sim, (si - 1 - int(d0["steps_since_sort"])) % si)
+    resorts = -(-args.steps // si) if si > 0 else 0
     # timed region: K full steps, CUDA events on the launching stream
     pic.pic_kernel_timing(sim, True)
-    sampler, rows = clock_sampler()
+    clk = NvmlClocks(local)
+    sampler, rows = (None, None) if clk.ok else clock_sampler()
     barrier()
+    launches0 = pic.pic_launch_count()
+    clk.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -725,13 +931,11 @@ def main():
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
-    clocks = clock_summary(sampler, rows)
+    clocks = clk.stop() if clk.ok else clock_summary(sampler, rows)
+    launches = pic.pic_launch_count() - launches0
     push_ms, push_launches = pic.pic_kernel_timing(sim, False)
     diag = pic.pic_diagnostics(sim)
     n_end = diag["n_particles"]
-    si = tuned["sort_interval"] if tuned else args.sort_interval
-    resorts = (args.steps + si - 1) // si if si else 0
-    launches = 4 * args.steps + 5 * resorts
 
     # end to end through the C ABI with host buffers: every step uploads the state from
     # pinned memory, steps and reads it back (pic_step_host)
@@ -763,7 +967,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": run_config(args, info["n_tris"], info["n_edges"], dt),
+            "config": run_config(args, info["n_tris"], info["n_edges"], dt, si),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_push_f32", "peak_kind": peak_kind,
@@ -773,7 +977,10 @@ def main():
                     "h2d_bytes_per_step": n_slots * bpp, "d2h_bytes_per_step": n_slots * bpp,
                     "steps": args.e2e_steps},
             "gpu_launches": launches,
+            "gpu_launches_counted": "kernels the library enqueued in the timed region "
+                                    "(pic_launch_count before and after)",
             "tuning": tuned,
+            "resorts_in_timed_region": resorts,
             "clocks": clocks,
             "checks": {"dt_over_stable": dt / dt_max,
                        "dce_nonzero_nodes": diag["dce_nonzero"], "dgl_drift": diag["dgl_drift"],
@@ -781,9 +988,13 @@ def main():
                        "absorbed": diag["n_absorbed"]},
         }
         if not args.no_cpu_baseline:
-            cb = cpu_baseline(wl, pusher=args.pusher)
-            cb.pop("seconds", None)
-            line["cpu_baseline"] = cb
+            line["cpu_baseline"] = cpu_baseline(wl, pusher=args.pusher)
+        if not args.no_extras:
+            line["m3u"] = measure_m3u(pic, mesh, wl, dt, peak)
+            del mesh
+            line["fp64"] = measure_fp64(pic, wl, dt, peak)
+            if args.batched:
+                line["batched"] = sweep_measure(args.batched, 64, 16)
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()

@@ -101,6 +101,9 @@ typedef struct {
     double q_absorbed;       /* charge removed at walls since creation (3D, q*w units)   */
     int64_t n_emitted;       /* particles born by the emitter since creation              */
     int64_t emit_dropped;    /* particles the emitter did not make for lack of capacity   */
+    int64_t steps_since_sort;/* steps since the last re-sort by triangle (the next one
+                                comes after the step that makes this sort_interval)     */
+    int64_t sort_interval;   /* steps between re-sorts now in force (0: never)          */
 } pic_diag;
 
 /* Allocator hook for device memory (e.g. a framework's caching allocator).  alloc must

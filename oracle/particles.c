@@ -17,6 +17,19 @@
 #include <math.h>
 #include <stdint.h>
 
+/* The plain build (the oracle the tests use) is single-threaded and these expand to
+ * nothing.  Built a second time with -fopenmp, for the timed CPU baseline only, the
+ * particle loop runs on all host cores and every accumulation into shared arrays is
+ * atomic (the order of the sums then varies between runs). */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORACLE_PARALLEL_FOR _Pragma("omp parallel for schedule(dynamic, 4096)")
+#define ORACLE_ATOMIC _Pragma("omp atomic")
+#else
+#define ORACLE_PARALLEL_FOR
+#define ORACLE_ATOMIC
+#endif
+
 enum { TAG_INTERIOR = 0, TAG_PEC = 1, TAG_AXIS = 2, TAG_ABSORB = 3 };
 
 typedef struct {
@@ -46,7 +59,7 @@ static void deposit_segment(const omesh *m, int t, const double ls[3], const dou
     for (int k = 0; k < 3; k++) {
         int a, b;
         edge_ends(n3, k, &a, &b);
-        J[m->tri_edges[3 * t + k]] += w * (ls[a] * le[b] - ls[b] * le[a]);
+        ORACLE_ATOMIC J[m->tri_edges[3 * t + k]] += w * (ls[a] * le[b] - ls[b] * le[a]);
     }
 }
 
@@ -158,6 +171,7 @@ int oracle_push(const int32_t *tri_nodes, const int32_t *tri_edges, const int32_
     omesh m = {tri_nodes, tri_edges, tri_nbr, tri_btag, node_zr, grad, area};
     const double h = 0.5 * qm * dt;
     const double wJ = q_src / dt;
+    ORACLE_PARALLEL_FOR
     for (int64_t p = 0; p < np; p++) {
         int t = tri[p];
         if (t < 0) continue;
@@ -233,7 +247,7 @@ int oracle_push(const int32_t *tri_nodes, const int32_t *tri_edges, const int32_
             lc[i] /= sum;
             lc[j] /= sum;
             deposit_segment(&m, t, l, lc, wJ, J);
-            counters[2]++;
+            ORACLE_ATOMIC counters[2]++;
             int nb = tri_nbr[3 * t + kx];
             int tag = tri_btag[3 * t + kx];
             if (nb < 0 && tag == TAG_AXIS) {
@@ -244,9 +258,9 @@ int oracle_push(const int32_t *tri_nodes, const int32_t *tri_edges, const int32_
             if (nb < 0 || ncross + 1 >= max_cross) {
                 /* absorbed at the wall (or walk cap reached): its charge leaves */
                 const int32_t *nn = tri_nodes + 3 * t;
-                for (int k = 0; k < 3; k++) Qabs[nn[k]] += q_src * lc[k];
-                if (nb >= 0) counters[1]++;
-                counters[0]++;
+                for (int k = 0; k < 3; k++) ORACLE_ATOMIC Qabs[nn[k]] += q_src * lc[k];
+                if (nb >= 0) ORACLE_ATOMIC counters[1]++;
+                ORACLE_ATOMIC counters[0]++;
                 alive = 0;
                 break;
             }
@@ -268,7 +282,7 @@ int oracle_push(const int32_t *tri_nodes, const int32_t *tri_edges, const int32_
         }
         if (alive) {
             const int32_t *nn = tri_nodes + 3 * t;
-            for (int k = 0; k < 3; k++) Q[nn[k]] += q_src * l[k];
+            for (int k = 0; k < 3; k++) ORACLE_ATOMIC Q[nn[k]] += q_src * l[k];
             tri[p] = t;
             lam[3 * p] = l[0];
             lam[3 * p + 1] = l[1];
@@ -278,6 +292,16 @@ int oracle_push(const int32_t *tri_nodes, const int32_t *tri_edges, const int32_
         }
     }
     return 0;
+}
+
+/* Host threads the particle loop runs on (1 in the plain build). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Eq. charge: Q_k += q_src * lambda_k for every live particle. */

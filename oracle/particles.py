@@ -15,6 +15,10 @@ WALK_CAP = 16   # edge crossings per particle per step before it is dropped
 BORIS, VAY = 0, 1   # velocity update of Eq. DLE (Sec. 3.3)
 
 
+_LIB_OMP = os.path.join(_HERE, "_liboracle_omp.so")
+_lib_omp = None
+
+
 def build_oracle_lib(force=False):
     """Compile particles.c with gcc (no fast-math, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
@@ -25,19 +29,50 @@ def build_oracle_lib(force=False):
     return _LIB
 
 
-def _load():
-    global _lib
+def build_oracle_omp_lib(force=False):
+    """The same source built with -fopenmp: the particle loop on all host cores with
+    atomic accumulators.  Only the timed CPU baseline uses it; returns None when the
+    compiler has no OpenMP."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + ".%d.tmp" % os.getpid()
+        r = subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                            "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def _declare(lib):
+    P = ctypes.c_void_p
+    lib.oracle_push.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int64, P, P, P, P, P, P, P]
+    lib.oracle_kick.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, ctypes.c_double,
+                                ctypes.c_double, P]
+    lib.oracle_deposit_charge.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double, P]
+    lib.oracle_threads.argtypes = []
+    return lib
+
+
+def _load(threads=False):
+    global _lib, _lib_omp
+    if threads:
+        if _lib_omp is None:
+            path = build_oracle_omp_lib()
+            if path is None:
+                raise RuntimeError("gcc without OpenMP: no multi-threaded oracle build")
+            _lib_omp = _declare(ctypes.CDLL(path))
+        return _lib_omp
     if _lib is None:
-        _lib = ctypes.CDLL(build_oracle_lib())
-        P = ctypes.c_void_p
-        _lib.oracle_push.argtypes = [P, P, P, P, P, P, P, P, P, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_int64, P, P, P, P, P, P, P]
-        _lib.oracle_kick.argtypes = [ctypes.c_int, ctypes.c_int64, P, P, P, ctypes.c_double,
-                                     ctypes.c_double, P]
-        _lib.oracle_deposit_charge.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double, P]
+        _lib = _declare(ctypes.CDLL(build_oracle_lib()))
     return _lib
+
+
+def host_threads(threads=False):
+    """Host threads the particle loop of the plain (1) or the OpenMP build runs on."""
+    return int(_load(threads).oracle_threads())
 
 
 def _ptr(a):
@@ -71,10 +106,11 @@ def kick(pusher, u, Ef, Bf, h, c):
 
 
 def push(pm, E, Bavg, bz, dt, qm, c, q_src, tri, lam, u, J, Q, Qabs, max_cross=WALK_CAP,
-         pusher=BORIS):
+         pusher=BORIS, threads=False):
     """One particle step in place (see oracle_push in particles.c).  Returns counters
-    (absorbed, walk-cap overflows, edge crossings)."""
-    lib = _load()
+    (absorbed, walk-cap overflows, edge crossings).  threads=True runs the OpenMP build
+    (all host cores, atomic sums; the timed CPU baseline only)."""
+    lib = _load(threads)
     for a, dt_ in ((tri, np.int32), (lam, np.float64), (u, np.float64), (J, np.float64),
                    (Q, np.float64), (Qabs, np.float64)):
         assert a.dtype == dt_ and a.flags.c_contiguous

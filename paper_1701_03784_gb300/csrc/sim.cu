@@ -1059,6 +1059,8 @@ struct SimImpl final : SimBase {
             o->n_particles = n_injected + (int64_t)cnt[CNT_EMITTED] - (int64_t)cnt[CNT_ABSORBED];
             o->n_emitted = (int64_t)cnt[CNT_EMITTED];
             o->emit_dropped = (int64_t)cnt[CNT_EMIT_DROPPED];
+            o->steps_since_sort = since_sort;
+            o->sort_interval = sort_interval;
             o->n_steps = n_steps;
             o->dce_max = out[0];
             o->dce_nonzero = (int64_t)out[1] + (int64_t)cnt[CNT_REMAINDER];

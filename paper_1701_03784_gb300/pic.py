@@ -41,7 +41,8 @@ class pic_diag(ctypes.Structure):
                 ("dce_nonzero", ctypes.c_int64), ("nr_dce_max", ctypes.c_double),
                 ("dgl_drift", ctypes.c_double), ("field_energy", ctypes.c_double),
                 ("kinetic_energy", ctypes.c_double), ("q_absorbed", ctypes.c_double),
-                ("n_emitted", ctypes.c_int64), ("emit_dropped", ctypes.c_int64)]
+                ("n_emitted", ctypes.c_int64), ("emit_dropped", ctypes.c_int64),
+                ("steps_since_sort", ctypes.c_int64), ("sort_interval", ctypes.c_int64)]
 
 
 class pic_emitter(ctypes.Structure):

@@ -435,3 +435,34 @@ def test_walk_cap_removes_the_particle_and_books_its_charge(cavity):
     assert out[0.9][0] == -1 and out[0.9][1][0] == 1 and out[0.9][1][1] == 1
     assert out[0.9][1][2] == TPart.WALK_CAP
     assert out[0.05][0] >= 0 and out[0.05][1][1] == 0 and 0 < out[0.05][1][2] < TPart.WALK_CAP
+
+
+def test_openmp_build_matches_the_plain_build(cavity):
+    """The timed CPU baseline runs particles.c built with -fopenmp (all host cores, atomic
+    sums).  Each particle's arithmetic is the same code, so positions, momenta, triangles
+    and counters agree exactly with the plain build; J, Q and Q_abs agree up to the order
+    of their sums."""
+    if TPart.build_oracle_omp_lib() is None:
+        pytest.skip("gcc without OpenMP")
+    m = cavity.mesh
+    pm = TPart.PushMesh(m)
+    rng = np.random.default_rng(5)
+    E = rng.uniform(-0.05, 0.05, m.N1)
+    Bavg = rng.uniform(-1e-3, 1e-3, m.N2)
+    z, r, ur, up, uz = W.uniform_in_mesh(m.nodes, m.tris, 20_000, 6, sigma_u=0.8)
+    tri0, lam0 = TPart.locate(m, z, r)
+    u0 = np.stack([ur, up, uz], 1)
+    out = []
+    for threads in (False, True):
+        tri, lam, u = tri0.astype(np.int32).copy(), lam0.copy(), u0.copy()
+        J, Q, Qa = np.zeros(m.N1), np.zeros(m.N0), np.zeros(m.N0)
+        cnt = TPart.push(pm, E, Bavg, 0.3, 0.5 * cavity.dt_max, -1.0, 1.0, 1e-3, tri, lam, u,
+                         J, Q, Qa, threads=threads)
+        out.append((tri, lam, u, J, Q, Qa, cnt))
+    a, b = out
+    for x, y in zip(a[:3] + a[6:], b[:3] + b[6:]):
+        assert np.array_equal(x, y)
+    assert a[6][2] > 0 and a[6][0] > 0
+    for x, y in zip(a[3:6], b[3:6]):
+        assert np.abs(x - y).max() <= 1e-12 * np.abs(x).max()
+    assert TPart.host_threads(True) >= 1 and TPart.host_threads(False) == 1
