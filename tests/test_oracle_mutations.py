@@ -140,8 +140,8 @@ C_CASES = [
      "if (kx < 0) { sx = s; kx = k; }",
      lambda cav: TP.test_multi_cell_current_is_the_line_integral_over_the_crossed_cells(cav)),
     ("charge: the new position's nodes given the old lambdas",
-     "for (int k = 0; k < 3; k++) Q[nn[k]] += q_src * l[k];",
-     "for (int k = 0; k < 3; k++) Q[nn[k]] += q_src * lam[3 * p + k];",
+     "for (int k = 0; k < 3; k++) ORACLE_ATOMIC Q[nn[k]] += q_src * l[k];",
+     "for (int k = 0; k < 3; k++) ORACLE_ATOMIC Q[nn[k]] += q_src * lam[3 * p + k];",
      lambda cav: TP.test_dce_exact_with_multi_cell_crossings(cav)),
     ("charge at injection: each node given its neighbour's lambda",
      "Q[tri_nodes[3 * t + k]] += q_src * lam[3 * p + k];",
@@ -160,8 +160,8 @@ C_CASES = [
      "if (nodes3[i] > nodes3[j]) { *a = i; *b = j; }",
      lambda cav: TP.test_uniform_E_kick(cav, 0)),
     ("wall: the absorbed charge not booked",
-     "for (int k = 0; k < 3; k++) Qabs[nn[k]] += q_src * lc[k];",
-     "for (int k = 0; k < 3; k++) Qabs[nn[k]] += 0.0 * lc[k];",
+     "for (int k = 0; k < 3; k++) ORACLE_ATOMIC Qabs[nn[k]] += q_src * lc[k];",
+     "for (int k = 0; k < 3; k++) ORACLE_ATOMIC Qabs[nn[k]] += 0.0 * lc[k];",
      lambda cav: TP.test_absorbed_charge_enters_dce(cav)),
 ]
 
