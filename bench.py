@@ -714,34 +714,62 @@ def run_staircase(args):
 
 
 def run_diode(args):
-    """Planar diode at 100 kV over 1 cm with a 6 cm emitter (Sec. 5.2's check on a planar
-    gap): the largest injection that forms no virtual cathode (no particle returns to the
-    cathode), bracketed by a scan of injection currents, against the classical
-    Child-Langmuir closed form; and the run's throughput."""
-    import torch
+    """Planar diode at 100 kV over 1 cm (Sec. 5.2's check on a planar gap): injection
+    scan against the relativistic planar space-charge-limited current -- the fraction
+    returned to the cathode (a virtual cathode) and the central current density that
+    crosses the gap -- on the planar check's setup (6 cm emitter in a 7 cm tube, 5 T guide
+    field, ~20k triangles graded toward the cathode, 2000 births per step, 10,000 +
+    10,000 steps); then the diode configuration as stated (1 cm disk, 2 cm tube, ~20k
+    uniform triangles, no guide field) over-injected, and its throughput."""
     import paper_1701_03784_gb300 as pkg
     pkg.build()
     from paper_1701_03784_gb300 import diode
+    from oracle import sources as OS
+    J_scl = OS.child_langmuir_planar(1e5, 1e-2, QE / ME, EPS0, C0)
+    J_cl = diode.classical_limit(1e5, 1e-2)
     rows = []
     t0 = time.perf_counter()
-    for f in (0.90, 0.95, 1.00, 1.05, 1.10, 1.20):
-        r = diode.run(over=f)
-        rows.append({"inject_over_classical": f, "return_fraction": r["return_fraction"],
+    for f in (0.9, 0.95, 1.0, 1.05, 1.1, 1.3):
+        r = diode.run(over=f * J_scl / J_cl)
+        rows.append({"inject_over_law": f, "return_fraction": r["return_fraction"],
+                     "J_center_over_law": r["J_center"] / J_scl,
                      "I_anode_over_I_emitted": r["I_anode"] / r["I_emitted"],
-                     "J_center_over_classical": r["J_center"] / r["J_classical"],
-                     "n_particles_end": r["n_particles"], "steps": r["steps"],
+                     "in_flight_end": r["n_particles"], "steps": r["steps"],
                      "emit_dropped": r["emit_dropped"], "dce_nonzero": r["dce_nonzero"]})
-    wall = time.perf_counter() - t0
-    clean = [x["inject_over_classical"] for x in rows if x["return_fraction"] == 0.0]
-    vc = [x["inject_over_classical"] for x in rows if x["return_fraction"] > 0.0]
-    print(json.dumps({"metric": "planar diode: space-charge limit bracket / classical "
-                                "Child-Langmuir", "unit": "ratio",
-                      "value": [max(clean) if clean else None, min(vc) if vc else None],
-                      "rows": rows, "wall_s": wall,
-                      "config": {"workload": "planar diode 100 kV, 1 cm gap, 7 cm wall, 6 cm "
-                                             "emitter, 35k triangles, 500 births per step, "
-                                             "FP32, 8000 + 6000 steps per injection"}}))
+    stated = diode.run(radius=2e-2, r_emit=1e-2, r_measure=0.3e-2, bz=0.0, grade=1.0,
+                       over=1.3 * J_scl / J_cl)
+    m2 = diode.throughput()
+    print(json.dumps({"metric": "planar diode: space-charge limit / relativistic Child-Langmuir",
+                      "unit": "ratio", "law_over_classical": J_scl / J_cl,
+                      "rows": rows, "wall_s": time.perf_counter() - t0,
+                      "stated_1cm_disk_over_1.3": {
+                          "J_center_over_law": stated["J_center"] / J_scl,
+                          "return_fraction": stated["return_fraction"],
+                          "in_flight_end": stated["n_particles"],
+                          "note": "a 1 cm disk 1 cm from the anode is a two-dimensional diode: "
+                                  "its limit exceeds the planar law (finite-emitter enhancement)"},
+                      "m2_throughput": m2,
+                      "config": {"workload": "planar diode 100 kV, 1 cm gap; scan: 6 cm emitter, "
+                                             "7 cm tube, 5 T, ~20k triangles graded to the "
+                                             "cathode (0.35), 2000 births per step, FP32, "
+                                             "10000 + 10000 steps per injection"}}))
     return 0
+
+
+M2_SETTLE = 4000
+
+
+def measure_m2():
+    """The diode configuration as stated (1 cm disk, 1 cm gap, 100 kV, ~20k triangles,
+    2000 births per step) once its gap has filled: throughput at that particle count."""
+    from paper_1701_03784_gb300 import diode
+    r = diode.throughput(settle_steps=M2_SETTLE)
+    r["workload"] = ("diode: 1 cm cathode disk, 1 cm gap, 100 kV, 2 cm tube, %d triangles, "
+                     "%d births per step at rest, FP32; timed after %d steps"
+                     % (r["n_tris"], r["births_per_step"], M2_SETTLE))
+    r["value"] = r.pop("particle_steps_per_s")
+    r["unit"] = "particle-steps/s"
+    return r
 
 
 def _timed_steps(pic, sim, steps):
@@ -993,6 +1021,7 @@ def main():
             line["m3u"] = measure_m3u(pic, mesh, wl, dt, peak)
             del mesh
             line["fp64"] = measure_fp64(pic, wl, dt, peak)
+            line["m2"] = measure_m2()
             if args.batched:
                 line["batched"] = sweep_measure(args.batched, 64, 16)
         print(json.dumps(line))

@@ -207,9 +207,21 @@ def bwo_small_mesh(n_tri=3000, seed=1012):
     return bwo_mesh(n_tri=n_tri, seed=seed, n_periods=2, guide=0.5e-2)
 
 
-def diode_mesh(n_tri=20_000, seed=1001, gap=1e-2, radius=2e-2):
-    """Planar diode: cathode plane z=0, anode plane z=gap, outer wall at rho=radius."""
-    return rect_mesh(gap, radius, n_tri, seed)
+def diode_mesh(n_tri=20_000, seed=1001, gap=1e-2, radius=2e-2, grade=1.0):
+    """Planar diode: cathode plane z=0, anode plane z=gap, outer wall at rho=radius.
+
+    grade < 1 compresses the cells toward the cathode: node z -> gap (g s + (1 - g) s^2),
+    s = z / gap, a monotone map that keeps rho, the two planes and the triangles'
+    orientation; the first cells are g times as deep (the space-charge-limited potential
+    varies as z^(4/3) there) and the last ones 2 - g times."""
+    nodes, tris, be, bt = rect_mesh(gap, radius, n_tri, seed)
+    if grade != 1.0:
+        s = nodes[:, 0] / gap
+        z = gap * (grade * s + (1.0 - grade) * s * s)
+        z[nodes[:, 0] == 0.0] = 0.0
+        z[nodes[:, 0] == gap] = gap
+        nodes = np.stack([z, nodes[:, 1]], 1)
+    return nodes, tris, be, bt
 
 
 def sws_cell_mesh(n_tri, seed=1020, staircase=False, r0=15.0e-3, ripple=2.1e-3,
