@@ -1,39 +1,64 @@
 // Surrogate network inference on the 5th-generation tensor cores: BF16 operands in shared
 // memory, FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA of 128 threads takes 128 samples of one ensemble member through every layer:
-//  * the activations (128 x K) and the layer's weights (N x K) sit in shared memory in the
-//    no-swizzle K-major layout (8 x 8 core matrices of 16-byte rows, K-adjacent core
-//    matrices 128 bytes apart, 8-row groups K/8 x 128 bytes apart);
-//  * one thread issues tcgen05.mma (kind::f16, M = 128, N = the padded layer width), 16
-//    of K at a time, accumulating a 128 x N FP32 tile in TMEM, and commits to an mbarrier;
-//  * each warp reads its 32 TMEM lanes (sample rows) with tcgen05.ld, adds the bias,
-//    applies the tanh-GELU (hidden layers) and writes the next layer's BF16 operand back
-//    into shared memory, or writes the FP32 outputs.
-// Every mbarrier wait is bounded (timeout counted, TMEM still freed).
+// One CTA takes two tiles of 128 samples of one ensemble member through every layer, in
+// ping-pong: while the tensor cores run one tile's products of a layer, the other tile's
+// epilogue of its previous layer runs on the CUDA cores.
+//  * the activations of each tile (128 x K) sit in shared memory in the no-swizzle
+//    K-major layout (8 x 8 core matrices of 16-byte rows, K-adjacent core matrices 128
+//    bytes apart, 8-row groups K/8 x 128 bytes apart); the layer's weights stream through
+//    a buffer of 128 output rows (a 128-row slice of the packed N x K weights is
+//    contiguous), loaded by a load warp as soon as the products that read the buffer have
+//    completed;
+//  * one thread of the control warp issues tcgen05.mma (kind::f16, M = 128, N = the rows of
+//    the slice, 16 of K at a time) into the tile's 128 x 256 FP32 accumulator in TMEM (the
+//    two accumulators fill TMEM's 512 columns), releasing each weight buffer with a
+//    commit and signalling the tile's epilogue with another after its last slice;
+//  * eight warps per tile (two per TMEM lane quadrant, each half the columns) read the
+//    accumulator with tcgen05.ld, add the bias, apply the tanh-GELU (hidden layers) and
+//    write the next layer's BF16 operand back into the tile, or write the FP32 outputs,
+//    then tell the control thread that the tile is ready for its next layer.
+// The layer-0 operand is built by the epilogue warps from the FP32 queries.  Every
+// mbarrier wait is bounded (timeout counted; the block then drains what it issued and
+// still frees TMEM).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstddef>
 
 #include "pic_internal.h"
 
 namespace pic {
 
 namespace {
-constexpr int TM = 128;       // samples per CTA = MMA M
-constexpr int NTH = 256;      // 8 warps: two per TMEM lane quadrant, each half the columns
+constexpr int TM = 128;       // samples per tile = MMA M
+constexpr int NTILE = 2;      // tiles per CTA (ping-pong)
+constexpr int EPI_WARPS = 8;  // per tile: two per TMEM lane quadrant, each half the columns
+constexpr int CTRL_WARP = NTILE * EPI_WARPS;   // lane 0 issues the products
+constexpr int LOAD_WARP = CTRL_WARP + 1;       // lane 0 streams the weights
+constexpr int NTH = (LOAD_WARP + 1) * 32;
 constexpr int KMAX = 256;
 constexpr int NMAX = 256;
-constexpr int TMEM_COLS = 256;
+constexpr int WROWS = 128;    // output rows per weight slice (N of each product)
+constexpr int NBUF = 1;       // weight buffers (two tiles' products hide a slice's load)
+constexpr int TMEM_COLS = 512;
+constexpr int BIAS_MAX = MLP_MAX_LAYERS * NMAX;
 constexpr long long WAIT_LIMIT = 1LL << 22;
 constexpr float C_GELU = 0.7978845608028654f;   // sqrt(2/pi)
 
-struct TcSmem {
-    uint16_t a[TM * KMAX];     // activations, core-matrix layout
-    uint16_t w[NMAX * KMAX];   // weights of the current layer, core-matrix layout
-    float bias[2][NMAX];       // biases of the current and the next layer
-    unsigned long long mbar;   // products of a layer done
-    unsigned long long wbar;   // weights and bias of a layer landed
+struct PingSmem {
+    uint16_t a[NTILE][TM * KMAX];        // activations of each tile, core-matrix layout
+    uint16_t w[NBUF][WROWS * KMAX];      // weight buffer(s) of 128 output rows
+    alignas(16) float bias[BIAS_MAX];    // every layer's bias of the member (bmember used)
+    unsigned long long wfull[NBUF];      // a weight buffer landed
+    unsigned long long wempty[NBUF];     // the products that read a weight buffer completed
+    unsigned long long accdone[NTILE];   // a tile's products of a layer completed
+    unsigned long long ready[NTILE];     // a tile's operand for its next layer is written
+    unsigned long long bbar;             // the biases landed
     unsigned int tmem;
 };
+static_assert(offsetof(PingSmem, w) % 1024 == 0 && offsetof(PingSmem, bias) % 16 == 0,
+              "bulk-copy destinations and operand tiles must stay aligned");
 
 // element offset of (row r, column k) in a core-matrix tile with kp (padded) columns
 __host__ __device__ __forceinline__ int core_off(int r, int k, int kp) {
@@ -87,12 +112,31 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
+// 16 consecutive FP32 columns of this thread's TMEM lane, issued without waiting: the
+// registers are valid after tmem_wait16 on them (which waits for every load in flight)
+__device__ __forceinline__ void tmem_issue16(unsigned taddr, unsigned (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait16(unsigned (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :: "memory");
+}
 __device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
-    for (long long k = 0; k < WAIT_LIMIT; k++) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity,
+                                          long long polls = WAIT_LIMIT) {
+    for (long long k = 0; k < polls; k++) {
         unsigned ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -120,40 +164,119 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
 __device__ __forceinline__ uint16_t bf16_bits(float x) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
-// 8 values as 8 BF16 in one 16-byte word (element 0 lowest)
-__device__ __forceinline__ uint4 pack8(const float *v) {
+// 8 values as 8 BF16 in one 16-byte word, two per conversion (element 0 lowest)
+__device__ __forceinline__ unsigned bf16x2_bits(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&h);
+}
+__device__ __forceinline__ uint4 pack8x2(const float *v) {
     uint4 q;
-    q.x = (unsigned)bf16_bits(v[0]) | ((unsigned)bf16_bits(v[1]) << 16);
-    q.y = (unsigned)bf16_bits(v[2]) | ((unsigned)bf16_bits(v[3]) << 16);
-    q.z = (unsigned)bf16_bits(v[4]) | ((unsigned)bf16_bits(v[5]) << 16);
-    q.w = (unsigned)bf16_bits(v[6]) | ((unsigned)bf16_bits(v[7]) << 16);
+    q.x = bf16x2_bits(v[0], v[1]);
+    q.y = bf16x2_bits(v[2], v[3]);
+    q.z = bf16x2_bits(v[4], v[5]);
+    q.w = bf16x2_bits(v[6], v[7]);
     return q;
 }
-// one thread: fetch layer l's weights (core-matrix layout, np x kp BF16) and bias (np FP32,
-// into bias buffer l % 2), completing on wbar
-__device__ __forceinline__ void load_layer(const MlpTc &tc, TcSmem &sm, int z, int l) {
-    const unsigned wb = (unsigned)(tc.np[l] * tc.kp[l] * 2), bb = (unsigned)(tc.np[l] * 4);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_u32(&sm.wbar)), "r"(wb + bb) : "memory");
-    bulk_load(sm.w, tc.w + (long long)z * tc.wmember + tc.woff[l], wb, &sm.wbar);
-    bulk_load(sm.bias[l & 1], tc.b + (long long)z * tc.bmember + tc.boff[l], bb, &sm.wbar);
+
+// Packed pairs of FP32 (element 0 in the low half): the epilogue's arithmetic runs two
+// columns per instruction on the FP32 pipes, and tanh two per instruction in FP16.
+__device__ __forceinline__ unsigned long long f2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(unsigned long long r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// tanh-GELU of a pair, returned as two BF16 (element 0 low): 0.5 z (1 + tanh(w)),
+// w = sqrt(2/pi) (z + 0.044715 z^3).  tanh is the hardware approximation on FP16 pairs
+// (absolute error about 2^-10.7, below the BF16 rounding of the result); the argument is
+// converted with saturation, so a huge |w| gives tanh = +-1.
+__device__ __forceinline__ unsigned gelu2_bf16(unsigned long long z) {
+    const unsigned long long k3 = f2(0.044715f, 0.044715f), one = f2(1.f, 1.f);
+    const unsigned long long kc = f2(C_GELU, C_GELU), half = f2(0.5f, 0.5f);
+    const unsigned long long w = mul2(mul2(z, kc), fma2(mul2(z, z), k3, one));
+    float w0, w1;
+    f2_split(w, w0, w1);
+    unsigned hw, ht;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(hw) : "f"(w1), "f"(w0));
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(ht) : "r"(hw));
+    const __half2 th = *reinterpret_cast<const __half2 *>(&ht);
+    const float2 t = __half22float2(th);
+    const unsigned long long hz = mul2(z, half);
+    float r0, r1;
+    f2_split(fma2(hz, f2(t.x, t.y), hz), r0, r1);
+    return bf16x2_bits(r0, r1);
 }
 
+// bias, GELU and BF16 of 16 accumulator columns c .. c+15 of row erow, written as the
+// next layer's operand (core-matrix layout, np columns)
+__device__ __forceinline__ void gelu_chunk(const unsigned (&r)[16], const float *bias, int c,
+                                           uint16_t *act, int erow, int np) {
+    const unsigned long long *bias2 = reinterpret_cast<const unsigned long long *>(bias + c);
+    unsigned p[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++)
+        p[j] = gelu2_bf16(add2(f2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])),
+                               bias2[j]));
+    *reinterpret_cast<uint4 *>(act + core_off(erow, c, np)) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4 *>(act + core_off(erow, c + 8, np)) = make_uint4(p[4], p[5], p[6], p[7]);
+}
+
+__device__ __forceinline__ void arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// The weight slices in the order the products use them: layer by layer, slice q = rows
+// [64q, 64q + 64) of the layer's packed N x K weights; both tiles' products read a slice
+// before the next one is needed, so each slice is loaded once per block.
+struct SliceIter {
+    int l = 0, q = 0;
+    __device__ __forceinline__ bool next(const MlpTc &tc) {
+        if (++q * WROWS < tc.np[l]) return true;
+        q = 0;
+        return ++l < tc.L;
+    }
+};
+
 __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, float *Y,
-                                                   long long n) {
+                                                   long long n, long long row_base) {
     extern __shared__ unsigned char raw[];
     const unsigned pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
-    TcSmem &sm = *reinterpret_cast<TcSmem *>(raw + pad);
+    PingSmem &sm = *reinterpret_cast<PingSmem *>(raw + pad);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int z = blockIdx.y;
-    const long long row0 = (long long)blockIdx.x * TM;
-    // epilogue: warp w reads TMEM lane quadrant w % 4 (rows) and half w / 4 of the columns
-    const int quad = warp & 3, half = warp >> 2;
-    const int erow = quad * 32 + lane;
+    // members run fastest along x, so that the blocks resident at one time read the
+    // weights of every member rather than all the same member's (the same lines)
+    const int z = blockIdx.x;
+    const long long pair0 = row_base + (long long)blockIdx.y * (NTILE * TM);
+    const long long polls = tc.wait_polls;
 
     if (tid == 0) {
-        mbar_init(&sm.mbar, 1);
-        mbar_init(&sm.wbar, 1);
+        for (int b = 0; b < NBUF; b++) {
+            mbar_init(&sm.wfull[b], 1);
+            mbar_init(&sm.wempty[b], 1);
+        }
+        for (int t = 0; t < NTILE; t++) {
+            mbar_init(&sm.accdone[t], 1);
+            mbar_init(&sm.ready[t], EPI_WARPS);
+        }
+        mbar_init(&sm.bbar, 1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -164,86 +287,165 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
     __syncthreads();
     fence_after();
     const unsigned tmem = sm.tmem;
-    if (tid == 0) load_layer(tc, sm, z, 0);
-    // layer-0 operand: one sample per thread of the first 128, BF16, zero-padded
-    if (tid < TM) {
-        const long long row = row0 + tid;
-        const int k0 = tc.k[0], kp = tc.kp[0];
-        for (int c = 0; c < kp; c += 8) {
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const int kk = c + j;
-                v[j] = row < n && kk < k0 ? X[row * k0 + kk] : 0.f;
-            }
-            *reinterpret_cast<uint4 *>(sm.a + core_off(tid, c, kp)) = pack8(v);
-        }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    fence_before();
-    __syncthreads();
-
     bool ok = true;
-    for (int l = 0; l < tc.L && ok; l++) {
-        const int kp = tc.kp[l], np = tc.np[l];
-        const bool last = l == tc.L - 1;
-        // the layer's weights and bias have landed
-        ok = __syncthreads_and(mbar_wait(&sm.wbar, (unsigned)(l & 1)));
-        if (!ok) break;
-        if (tid == 0) {
-            fence_after();
-            const unsigned a0 = smem_u32(sm.a), w0 = smem_u32(sm.w);
-            const unsigned sbo = (unsigned)kp / 8u * 128u;
-            const unsigned id = idesc_bf16(np);
-            for (int kk = 0; kk < kp / 16; kk++)
-                mma_bf16(tmem, sdesc(a0 + kk * 256u, 128u, sbo), sdesc(w0 + kk * 256u, 128u, sbo),
-                         id, kk > 0);
-            mma_commit(&sm.mbar);
+
+    if (warp == LOAD_WARP) {
+        // ---- weights (and once, the biases) ------------------------------------------
+        if (lane == 0) {
+            const unsigned bb = (unsigned)(tc.bmember * 4);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         ::"r"(smem_u32(&sm.bbar)), "r"(bb) : "memory");
+            bulk_load(sm.bias, tc.b + (long long)z * tc.bmember, bb, &sm.bbar);
+            SliceIter it;
+            long long c = 0;
+            do {
+                const int b = (int)(c % NBUF);
+                // the products that read this buffer NBUF slices ago have completed
+                if (c >= NBUF &&
+                    !mbar_wait(&sm.wempty[b], (unsigned)(((c - NBUF) / NBUF) & 1), polls)) {
+                    ok = false;
+                    break;
+                }
+                const int kp = tc.kp[it.l];
+                const int rows = min(WROWS, tc.np[it.l] - it.q * WROWS);
+                const unsigned wb = (unsigned)(rows * kp * 2);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             ::"r"(smem_u32(&sm.wfull[b])), "r"(wb) : "memory");
+                // in copies of 16 rows (8-row groups are contiguous), all in flight at once
+                const uint16_t *src = tc.w + (long long)z * tc.wmember + tc.woff[it.l] +
+                                      (long long)it.q * WROWS * kp;
+                for (int r0 = 0; r0 < rows; r0 += 16)
+                    bulk_load(sm.w[b] + r0 * kp, src + (long long)r0 * kp,
+                              (unsigned)(16 * kp * 2), &sm.wfull[b]);
+                c++;
+            } while (it.next(tc));
+            // before the block exits, every copy issued here has landed
+            const long long last = c;
+            for (long long k = last > NBUF ? last - NBUF : 0; k < last; k++)
+                mbar_wait(&sm.wfull[k % NBUF], (unsigned)((k / NBUF) & 1));
+            mbar_wait(&sm.bbar, 0);
         }
-        ok = __syncthreads_and(mbar_wait(&sm.mbar, (unsigned)(l & 1)));
-        if (!ok) break;
-        fence_after();
-        // the products are done with the weight buffer: fetch the next layer's during the
-        // epilogue (its bias goes to the other bias buffer)
-        if (tid == 0 && !last) load_layer(tc, sm, z, l + 1);
-        const float *bias = sm.bias[l & 1];
-        const int chunks = np / 16, c0 = half ? (chunks + 1) / 2 : 0;
-        const int c1 = half ? chunks : (chunks + 1) / 2;
-        const long long row = row0 + erow;
-        for (int ch = c0; ch < c1; ch++) {
-            const int c = ch * 16;
-            float v[16];
-            tmem_ld16(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)c, v);
+    } else if (warp == CTRL_WARP) {
+        // ---- products --------------------------------------------------------------------
+        if (lane == 0) {
+            SliceIter it;
+            long long c = 0;
+            bool first = true;
+            do {
+                const int l = it.l, kp = tc.kp[l];
+                const int b = (int)(c % NBUF);
+                if (!mbar_wait(&sm.wfull[b], (unsigned)((c / NBUF) & 1), polls)) {
+                    ok = false;
+                    break;
+                }
+                const int rows = min(WROWS, tc.np[l] - it.q * WROWS);
+                const bool last_slice = (it.q + 1) * WROWS >= tc.np[l];
+                const unsigned w0 = smem_u32(sm.w[b]);
+                const unsigned sbo = (unsigned)kp / 8u * 128u;
+                const unsigned id = idesc_bf16(rows);
+                for (int t = 0; t < NTILE && ok; t++) {
+                    // a tile's first slice of a layer waits for its operand (and for its
+                    // accumulator to have been read)
+                    if (it.q == 0 && !mbar_wait(&sm.ready[t], (unsigned)(l & 1), polls)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const unsigned a0 = smem_u32(sm.a[t]);
+                    const unsigned d = tmem + (unsigned)(t * 256 + it.q * WROWS);
+                    for (int kk = 0; kk < kp / 16; kk++)
+                        mma_bf16(d, sdesc(a0 + kk * 256u, 128u, sbo),
+                                 sdesc(w0 + kk * 256u, 128u, sbo), id, kk > 0);
+                    if (last_slice) mma_commit(&sm.accdone[t]);
+                    first = false;
+                }
+                if (!ok) break;
+                mma_commit(&sm.wempty[b]);
+                c++;
+            } while (it.next(tc));
+            // the products in flight complete before the block frees TMEM
+            if (!first) {
+                mma_commit(&sm.wempty[c % NBUF]);
+                mbar_wait(&sm.wempty[c % NBUF], (unsigned)((c / NBUF) & 1));
+            }
+        }
+    } else {
+        // ---- epilogues: warps 8t .. 8t+7 own tile t ----------------------------------------
+        const int t = warp / EPI_WARPS, w = warp % EPI_WARPS;
+        const int quad = w & 3, half = w >> 2;
+        const int erow = quad * 32 + lane;
+        const long long row = pair0 + (long long)t * TM + erow;
+        uint16_t *act = sm.a[t];
+        // layer-0 operand: the two warps of a quadrant split its 32 rows' columns
+        {
+            const int k0 = tc.k[0], kp = tc.kp[0];
+            for (int cc = half * 8; cc < kp; cc += 16) {
+                float v[8];
 #pragma unroll
-            for (int j = 0; j < 16; j++) v[j] += bias[c + j];
-            if (!last) {
-#pragma unroll
-                for (int j = 0; j < 16; j++) v[j] = gelu_approx(v[j]);
-                *reinterpret_cast<uint4 *>(sm.a + core_off(erow, c, np)) = pack8(v);
-                *reinterpret_cast<uint4 *>(sm.a + core_off(erow, c + 8, np)) = pack8(v + 8);
-            } else if (row < n) {
-                const int nout = tc.n[l];
-#pragma unroll
-                for (int j = 0; j < 16; j++)
-                    if (c + j < nout) Y[((long long)z * n + row) * nout + c + j] = v[j];
+                for (int j = 0; j < 8; j++) {
+                    const int kk = cc + j;
+                    v[j] = row < n && kk < k0 ? X[row * k0 + kk] : 0.f;
+                }
+                *reinterpret_cast<uint4 *>(act + core_off(erow, cc, kp)) = pack8x2(v);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        fence_before();
-        __syncthreads();
-    }
-    if (!ok) {
-        // a wait gave up: count it, give the copies and products in flight one more bounded
-        // wait, free TMEM below
-        if (tid == 0) {
-            atomicAdd(tc.err, 1u);
-            mbar_wait(&sm.wbar, 0);
-            mbar_wait(&sm.wbar, 1);
-            mbar_wait(&sm.mbar, 0);
-            mbar_wait(&sm.mbar, 1);
+        __syncwarp();
+        if (lane == 0) arrive(&sm.ready[t]);
+        ok = mbar_wait(&sm.bbar, 0, polls);
+        for (int l = 0; l < tc.L && ok; l++) {
+            const int np = tc.np[l];
+            const bool last = l == tc.L - 1;
+            if (!mbar_wait(&sm.accdone[t], (unsigned)(l & 1), polls)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const float *bias = sm.bias + tc.boff[l];
+            const int chunks = np / 16, c0 = half ? (chunks + 1) / 2 : 0;
+            const int c1 = half ? chunks : (chunks + 1) / 2;
+            const unsigned lane_base = tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(t * 256);
+            if (!last && c0 < c1) {
+                // hidden layer: the next chunk's TMEM load is in flight while this one is
+                // computed (two register sets, alternating)
+                unsigned ra[16], rb[16];
+                tmem_issue16(lane_base + (unsigned)(c0 * 16), ra);
+                tmem_wait16(ra);
+                for (int ch = c0; ch < c1; ch += 2) {
+                    if (ch + 1 < c1) tmem_issue16(lane_base + (unsigned)((ch + 1) * 16), rb);
+                    gelu_chunk(ra, bias, ch * 16, act, erow, np);
+                    if (ch + 1 >= c1) break;
+                    tmem_wait16(rb);
+                    if (ch + 2 < c1) tmem_issue16(lane_base + (unsigned)((ch + 2) * 16), ra);
+                    gelu_chunk(rb, bias, (ch + 1) * 16, act, erow, np);
+                    if (ch + 2 < c1) tmem_wait16(ra);
+                }
+            }
+            for (int ch = last ? c0 : c1; ch < c1; ch++) {
+                const int c = ch * 16;
+                float v[16];
+                tmem_ld16(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(t * 256 + c), v);
+                if (row < n) {
+                    const int nout = tc.n[l];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) v[j] += bias[c + j];
+#pragma unroll
+                    for (int j = 0; j < 16; j++)
+                        if (c + j < nout) Y[((long long)z * n + row) * nout + c + j] = v[j];
+                }
+            }
+            if (!last) {
+                // the operand is written and the accumulator read: the tile's next layer
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_before();
+                __syncwarp();
+                if (lane == 0) arrive(&sm.ready[t]);
+            }
         }
-        __syncthreads();
     }
+    if (!ok) atomicAdd(tc.err, 1u);
+    fence_before();
+    __syncthreads();
     fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -418,12 +620,22 @@ bool mlp_tc_gemm(const TcGemmOp &g, int E, uint16_t *scratch_a, uint16_t *scratc
 
 pic_status mlp_tc_forward(const MlpTc &tc, const float *X, float *Y, int64_t n, cudaStream_t s) {
     if (n <= 0) return PIC_OK;
-    const int smem = (int)sizeof(TcSmem) + 1024;
+    if (tc.bmember > BIAS_MAX) {
+        set_error("pic_mlp_forward: %lld biases per member, the tensor-core path holds %d",
+                  tc.bmember, BIAS_MAX);
+        return PIC_ERR_ARG;
+    }
+    const int smem = (int)sizeof(PingSmem) + 1024;
     PIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PIC_CUDA_TRY(cudaMemsetAsync(tc.err, 0, sizeof(unsigned int), s));
-    dim3 grid((unsigned)((n + TM - 1) / TM), (unsigned)tc.E);
-    k_mlp_tc<<<grid, NTH, smem, s>>>(tc, X, Y, (long long)n);
-    PIC_LAUNCHED();
+    // grid: members along x, pairs of tiles along y (at most 65535 pairs per launch)
+    const long long pairs = (n + NTILE * TM - 1) / (NTILE * TM);
+    for (long long p0 = 0; p0 < pairs; p0 += 65535) {
+        const long long np_ = std::min<long long>(65535, pairs - p0);
+        k_mlp_tc<<<dim3((unsigned)tc.E, (unsigned)np_), NTH, smem, s>>>(tc, X, Y, (long long)n,
+                                                                        p0 * NTILE * TM);
+        PIC_LAUNCHED();
+    }
     PIC_CUDA_TRY(cudaGetLastError());
     unsigned int err = 0;
     PIC_CUDA_TRY(cudaMemcpyAsync(&err, tc.err, sizeof(err), cudaMemcpyDeviceToHost, s));

@@ -60,6 +60,7 @@ struct MlpTc {
     uint16_t *w = nullptr;                                  // E * wmember BF16
     float *b = nullptr;                                     // E * bmember
     unsigned int *err = nullptr;                            // bounded-wait timeouts
+    long long wait_polls = 1LL << 22;                       // polls of a pipeline wait
     bool ok = false;
 };
 // FP32 parameters (per member: W_l (n x k), b_l at woff / boff, member stride P) -> tc

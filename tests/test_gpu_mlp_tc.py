@@ -40,3 +40,22 @@ def test_tensor_core_forward_matches_reference(env, n):
         assert np.abs(Yt[e] - y).max() <= 3e-2 * scale, e
         assert np.abs(Yf[e] - y).max() <= 1e-5 * scale, e
         assert np.sqrt(np.mean((Yt[e] - y) ** 2)) <= 1e-2 * np.sqrt(np.mean(y ** 2)), e
+
+
+@pytest.mark.parametrize("sizes", [(6, 96, 48, 200, 33), (3, 16, 5)])
+def test_tensor_core_forward_uneven_widths(env, sizes):
+    """Widths that are not multiples of the 64-row weight slices: a layer's last slice
+    has 32, 16 or 48 rows (padded widths 96, 48, 208), and a one-hidden-layer network."""
+    pic, torch = env
+    E, n = 3, 700
+    m = pic.pic_mlp_create(E, sizes, 256)
+    nets = members(E, sizes, seed=31)
+    pic.pic_mlp_params_set(m, np.stack([flat(W, b) for W, b in nets]))
+    x = np.random.default_rng(32).uniform(-1, 1, (n, sizes[0]))
+    X = torch.tensor(x, dtype=torch.float32, device="cuda")
+    Yt = pic.pic_mlp_forward(m, X, tensor_cores=True).cpu().numpy()
+    for e, (W, b) in enumerate(nets):
+        y, _ = mlp.forward(W, b, x)
+        scale = np.abs(y).max()
+        assert np.abs(Yt[e] - y).max() <= 3e-2 * scale, e
+        assert np.sqrt(np.mean((Yt[e] - y) ** 2)) <= 1e-2 * np.sqrt(np.mean(y ** 2)), e
