@@ -256,8 +256,7 @@ pic_status pic_sim_set_emitter(pic_sim *s, const pic_emitter *e, void *cuda_stre
 pic_status pic_sim_set_loss(pic_sim *s, const double *sigma_e, const double *sigma_m,
                             void *cuda_stream);
 
-/* Field probes recorded on the device (the output-port signal of Sec. 5.3, field energy
- * envelopes): n_entries (face, group, weight) triples; after the B update of a step,
+/* Field probes recorded on the device (field values and energy envelopes): n_entries (face, group, weight) triples; after the B update of a step,
  * group g sums weight * B_f (power[g] = 1) or weight * B_f^2 (power[g] = 2) over its
  * entries, B being B^{n+1/2}.  Every `every` steps, counted from this call, the n_groups
  * sums are appended to a device buffer of `capacity` records; nothing else waits for the
@@ -274,6 +273,29 @@ pic_status pic_sim_set_probes(pic_sim *s, int64_t n_entries, const int32_t *face
  * or did not fit cap_records.  Synchronous.  Errors: STATE (no probes), CUDA. */
 pic_status pic_probes_read(pic_sim *s, double *out, int64_t cap_records, int64_t *n_records,
                            int64_t *n_dropped, void *cuda_stream);
+
+/* Output-port signal recorded on the device: the BWO's output power (Secs. 5.1, 5.1.1),
+ * as the Poynting flux through planes z = z[k], rho0[k] <= rho <= rho1[k]:
+ *   P_k = (2 pi / mu0) int_rho0^rho1 E_rho B_phi rho drho,
+ * with E^n (Whitney 1-form, the static field included when one is set) and the
+ * time-centred B_phi = (B^{n+1/2} + B^{n-1/2}) / (2 A) (Whitney 2-form) of step n, the
+ * fields the gather of that step sees.  Each plane is cut into the chords of the triangles
+ * it crosses; E_rho and rho are linear along a chord and B_phi is constant, so two
+ * Gauss-Legendre points per chord give the integral of the discrete fields exactly.
+ * Positive P flows toward +z.  Every `every` steps, counted from this call, the n_ports
+ * values are appended to a device buffer of `capacity` records (nothing waits for the
+ * host; graph replay records too).  n_ports = 0 removes the ports.  Errors: ARG (a plane
+ * that does not cross the mesh in one piece between rho0 and rho1, or passes through a
+ * node; bad sizes), OOM, CUDA.  Units: watts for SI fields. */
+pic_status pic_sim_set_ports(pic_sim *s, int32_t n_ports, const double *z, const double *rho0,
+                             const double *rho1, int64_t capacity, int32_t every,
+                             void *cuda_stream);
+
+/* Copy out the port records made since the last read (at most cap_records x n_ports
+ * doubles, record-major) and start a new set; as pic_probes_read.  Errors: STATE (no
+ * ports), CUDA. */
+pic_status pic_ports_read(pic_sim *s, double *out, int64_t cap_records, int64_t *n_records,
+                          int64_t *n_dropped, void *cuda_stream);
 
 /* Replay steps from a CUDA graph (off by default).  pic_step then records one period of
  * 2 x the re-sort interval steps (2 with re-sorting off) on an internal stream the first

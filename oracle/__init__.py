@@ -18,6 +18,8 @@ Layout:
   sources.py    static gun field (Laplace problem), cathode emission with counter-based
                 draws, planar space-charge-limited current (Secs. 5.2, 5.3).
   mlp.py        the surrogate network: forward, backward and Adam, written out plainly.
+  port.py       output-port power: the Poynting flux of the discrete fields through a
+                plane (Secs. 5.1, 5.1.1).
 
 Every function's pin (what fixes it other than itself) is in tests/test_oracle_*.py;
 tests/test_oracle_mutations.py plants one mistake at a time in a copy of a routine here

@@ -312,6 +312,27 @@ struct ProbeArgs {
 template <class P>
 void launch_probe(const ProbeArgs<P> &a, cudaStream_t s);
 
+// output ports: port k owns entries [ptr[k], ptr[k+1]) of (triangle, barycentric point,
+// quadrature weight); after the face kernel of a step, P_k = sum w E_rho(lambda) B_phi
+// from the triangle records (E^n and the time-centred B_phi); every `every` steps the
+// ports' values are appended to a device buffer; state as for the probes
+template <class P>
+struct PortArgs {
+    const TriRec<typename P::R> *rec;
+    const int64_t *ptr;
+    const int32_t *tri;
+    const double *lam;      // 3 per entry
+    const double *weight;
+    double *buf;            // capacity x n_ports
+    long long *state;
+    unsigned *done;
+    int32_t n_ports, every;
+    long long capacity;
+};
+
+template <class P>
+void launch_port(const PortArgs<P> &a, cudaStream_t s);
+
 template <class P>
 struct FieldArgs {
     TriRec<typename P::R> *rec;

@@ -89,6 +89,11 @@ struct SimBase {
                                   int64_t capacity, int32_t every, cudaStream_t s) = 0;
     virtual pic_status probes_read(double *out, int64_t cap, int64_t *n_rec, int64_t *n_drop,
                                    cudaStream_t s) = 0;
+    virtual pic_status set_ports(int32_t n, const double *z, const double *rho0,
+                                 const double *rho1, int64_t capacity, int32_t every,
+                                 cudaStream_t s) = 0;
+    virtual pic_status ports_read(double *out, int64_t cap, int64_t *n_rec, int64_t *n_drop,
+                                  cudaStream_t s) = 0;
     int32_t sort_interval = 16;
     int32_t pusher = PIC_PUSHER_BORIS;
     int64_t wait_polls = PUSH_WAIT_POLLS;   // particle kernel's tile-pipeline waits
@@ -144,6 +149,9 @@ struct SimImpl final : SimBase {
     // field probes recorded on the device
     ProbeArgs<P> probe{};
     bool probes_on = false;
+    // output ports recorded on the device
+    PortArgs<P> port{};
+    bool ports_on = false;
 
     bool timing_on = false;
     // host round trips (step_host): uploads and downloads run on streams of their own,
@@ -469,6 +477,85 @@ struct SimImpl final : SimBase {
         PIC_CUDA_TRY(cudaStreamSynchronize(s));
         if (n_rec) *n_rec = rec;
         if (n_drop) *n_drop = st3[2] + (st3[1] - rec);
+        return PIC_OK;
+    }
+
+    // Output ports: for each plane z_k, the chords of the triangles it crosses between
+    // rho0_k and rho1_k (the emission line's tabulation), two Gauss-Legendre points per
+    // chord with weights (2 pi / mu0) (rho_b - rho_a) / 2 rho.
+    pic_status set_ports(int32_t n, const double *z, const double *rho0, const double *rho1,
+                         int64_t capacity, int32_t every, cudaStream_t s) override {
+        src_version++;
+        if (n <= 0) {
+            ports_on = false;
+            return PIC_OK;
+        }
+        if (!z || !rho0 || !rho1 || capacity < 1 || every < 1) {
+            set_error("pic_sim_set_ports: bad argument");
+            return PIC_ERR_ARG;
+        }
+        const double gp = 0.5 / std::sqrt(3.0);
+        const double pi2_mu = 2.0 * M_PI / m->units.mu0;
+        std::vector<int64_t> ptr(n + 1, 0);
+        std::vector<int32_t> tri;
+        std::vector<double> lam, w;
+        for (int32_t k = 0; k < n; k++) {
+            std::vector<double> ra, rb, la, lb;
+            std::vector<int32_t> tr;
+            if (!std::isfinite(z[k]) || !(rho1[k] > rho0[k]) || rho0[k] < 0.0 ||
+                !build_emit_line(*m, z[k], rho0[k], rho1[k], ra, rb, la, lb, tr)) {
+                set_error("pic_sim_set_ports: port %d (z = %g, rho in [%g, %g]) does not cross "
+                          "the mesh in one piece", (int)k, z[k], rho0[k], rho1[k]);
+                return PIC_ERR_ARG;
+            }
+            for (size_t i = 0; i < tr.size(); i++) {
+                for (int g = 0; g < 2; g++) {
+                    const double f = g == 0 ? 0.5 - gp : 0.5 + gp;
+                    const double rho = ra[i] + f * (rb[i] - ra[i]);
+                    tri.push_back(tr[i]);
+                    for (int c = 0; c < 3; c++)
+                        lam.push_back(la[3 * i + c] + f * (lb[3 * i + c] - la[3 * i + c]));
+                    w.push_back(pi2_mu * 0.5 * (rb[i] - ra[i]) * rho);
+                }
+            }
+            ptr[k + 1] = (int64_t)tri.size();
+        }
+        int64_t *d_ptr;
+        int32_t *d_tri;
+        double *d_lam, *d_w, *d_buf;
+        long long *d_state;
+        unsigned *d_done;
+        pic_status st;
+        if ((st = upload(d_ptr, ptr)) || (st = upload(d_tri, tri)) || (st = upload(d_lam, lam)) ||
+            (st = upload(d_w, w)) || (st = dalloc(d_buf, capacity * (int64_t)n)) ||
+            (st = dalloc(d_state, 3)) || (st = dalloc(d_done, 1)))
+            return st;
+        PIC_CUDA_TRY(cudaMemsetAsync(d_state, 0, 3 * sizeof(long long), s));
+        PIC_CUDA_TRY(cudaMemsetAsync(d_done, 0, sizeof(unsigned), s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        port = PortArgs<P>{rec, d_ptr, d_tri, d_lam, d_w, d_buf, d_state, d_done, n, every,
+                           (long long)capacity};
+        ports_on = true;
+        return PIC_OK;
+    }
+
+    pic_status ports_read(double *out, int64_t cap_rec, int64_t *n_rec, int64_t *n_drop,
+                          cudaStream_t s) override {
+        if (!ports_on) {
+            set_error("pic_ports_read: no ports set");
+            return PIC_ERR_STATE;
+        }
+        long long st3[3];
+        PIC_CUDA_TRY(cudaMemcpyAsync(st3, port.state, sizeof st3, cudaMemcpyDeviceToHost, s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        const int64_t rec_n = std::min<int64_t>(st3[1], cap_rec);
+        if (out && rec_n > 0)
+            PIC_CUDA_TRY(cudaMemcpyAsync(out, port.buf, sizeof(double) * rec_n * port.n_ports,
+                                         cudaMemcpyDeviceToHost, s));
+        PIC_CUDA_TRY(cudaMemsetAsync(port.state + 1, 0, 2 * sizeof(long long), s));
+        PIC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (n_rec) *n_rec = rec_n;
+        if (n_drop) *n_drop = st3[2] + (st3[1] - rec_n);
         return PIC_OK;
     }
 
@@ -934,6 +1021,7 @@ struct SimImpl final : SimBase {
             fa.Qnext = Qnext;
             launch_field_b<P>(fa, s);
             if (probes_on) launch_probe<P>(probe, s);
+            if (ports_on) launch_port<P>(port, s);
             PushArgs<P> pa;
             pa.rec = rec;
             pa.p = parts[cur];
@@ -1481,6 +1569,21 @@ extern "C" pic_status pic_probes_read(pic_sim *s, double *out, int64_t cap_recor
     return s->impl->probes_read(out, cap_records, n_records, n_dropped, (cudaStream_t)st);
 }
 PIC_CATCH("pic_probes_read")
+
+extern "C" pic_status pic_sim_set_ports(pic_sim *s, int32_t n_ports, const double *z,
+                                        const double *rho0, const double *rho1, int64_t capacity,
+                                        int32_t every, void *st) try {
+    SIM_CHECK(s, "pic_sim_set_ports");
+    return s->impl->set_ports(n_ports, z, rho0, rho1, capacity, every, (cudaStream_t)st);
+}
+PIC_CATCH("pic_sim_set_ports")
+
+extern "C" pic_status pic_ports_read(pic_sim *s, double *out, int64_t cap_records,
+                                     int64_t *n_records, int64_t *n_dropped, void *st) try {
+    SIM_CHECK(s, "pic_ports_read");
+    return s->impl->ports_read(out, cap_records, n_records, n_dropped, (cudaStream_t)st);
+}
+PIC_CATCH("pic_ports_read")
 
 extern "C" pic_status pic_fields_set(pic_sim *s, const double *E, const double *B, void *st) try {
     SIM_CHECK(s, "pic_fields_set");

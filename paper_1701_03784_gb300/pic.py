@@ -81,6 +81,8 @@ _SIGS = {
     "pic_sim_set_loss": [_P, _P, _P, _P],
     "pic_sim_set_probes": [_P, _I64, _P, _P, _P, _I32, _P, _I64, _I32, _P],
     "pic_probes_read": [_P, _P, _I64, _P, _P, _P],
+    "pic_sim_set_ports": [_P, _I32, _P, _P, _P, _I64, _I32, _P],
+    "pic_ports_read": [_P, _P, _I64, _P, _P, _P],
     "pic_sim_set_graph": [_P, _I32],
     "pic_sim_autotune": [_P, _I32, _P, _P],
     "pic_mlp_create": [_I32, _I32, _P, _I32, _P],
@@ -374,6 +376,34 @@ def pic_probes_read(sim, stream=None):
     _check(_lib.pic_probes_read(sim.ptr, _ptr(out), len(out), ctypes.byref(n),
                                 ctypes.byref(d), _stream(stream)), "pic_probes_read")
     return out[:n.value].copy(), d.value
+
+
+def pic_sim_set_ports(sim, z, rho0, rho1, capacity, every=1, stream=None):
+    """Output-port power (Poynting flux through planes z[k], rho0[k]..rho1[k]) recorded on
+    the device every `every` steps; z = None removes the ports."""
+    if z is None:
+        _check(_lib.pic_sim_set_ports(sim.ptr, 0, None, None, None, 1, 1, _stream(stream)),
+               "pic_sim_set_ports")
+        sim._ports = 0
+        return
+    z = _arr(np.atleast_1d(z), np.float64)
+    r0 = _arr(np.broadcast_to(rho0, z.shape), np.float64)
+    r1 = _arr(np.broadcast_to(rho1, z.shape), np.float64)
+    _check(_lib.pic_sim_set_ports(sim.ptr, len(z), _ptr(z), _ptr(r0), _ptr(r1), int(capacity),
+                                  int(every), _stream(stream)), "pic_sim_set_ports")
+    sim._ports = len(z)
+    sim._port_cap = int(capacity)
+
+
+def pic_ports_read(sim, stream=None):
+    """(records x n_ports array of port powers since the last read, records dropped)."""
+    n = getattr(sim, "_ports", 0)
+    cap = getattr(sim, "_port_cap", 0)
+    out = np.zeros((max(cap, 1), max(n, 1)))
+    nr, nd = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.pic_ports_read(sim.ptr, _ptr(out), cap, ctypes.byref(nr), ctypes.byref(nd),
+                               _stream(stream)), "pic_ports_read")
+    return out[:nr.value, :n].copy(), nd.value
 
 
 def pic_sim_set_pusher(sim, pusher):

@@ -22,6 +22,7 @@ from oracle import operators as OO
 from oracle import particles as OP
 from oracle import sim as OS
 from oracle import sources as OSrc
+from oracle import port as OPort
 
 TP = importlib.import_module("test_oracle_particles")
 TO = importlib.import_module("test_oracle_operators")
@@ -30,6 +31,7 @@ TS = importlib.import_module("test_oracle_sources")
 TM = importlib.import_module("test_oracle_mlp")
 TL = importlib.import_module("test_oracle_layer")
 TF = importlib.import_module("test_oracle_fields")
+TPo = importlib.import_module("test_oracle_port")
 
 
 def _patch_py(monkeypatch, owner, name, old, new, importers=()):
@@ -341,7 +343,23 @@ PY_CASES = [
     ("Adam: no bias correction of the first moment", OM, "adam",
      "mh = mm / (1 - b1 ** step)", "mh = mm", (),
      lambda cav: TM.test_adam_first_step_is_signed_learning_rate(), None),
+    ("port: the rho of the flux element left out", OPort, "port_power",
+     "* r for r in (a, 0.5 * (a + b), b)]", "for r in (a, 0.5 * (a + b), b)]", (),
+     lambda cav: TPo.test_uniform_fields_give_the_closed_form(_port_guide(), 0.1, 0.37), None),
+    ("port: the W1 terms of an edge in the wrong order", OPort, "e_rho",
+     "(lam[a] * g[b, 1] - lam[b] * g[a, 1])", "(lam[b] * g[a, 1] - lam[a] * g[b, 1])", (),
+     lambda cav: TPo.test_uniform_fields_give_the_closed_form(_port_guide(), 0.0, 0.5), None),
+    ("port: B_phi without 1/A", OPort, "port_power",
+     "bphi = B[t] / mesh.area[t]", "bphi = B[t]", (),
+     lambda cav: TPo.test_uniform_fields_give_the_closed_form(_port_guide(), 0.0, 0.5), None),
+    ("port: the chord's midpoint weighted 2 instead of 4", OPort, "port_power",
+     "(f[0] + 4.0 * f[1] + f[2])", "(f[0] + 2.0 * f[1] + f[2])", (),
+     lambda cav: TPo.test_linear_in_z_field_gives_its_value_at_the_plane(_port_guide()), None),
 ]
+
+
+def _port_guide():
+    return OO.Mesh(*W.rect_mesh(1.0, 0.5, 1200, 17))
 
 
 @pytest.mark.parametrize("case", PY_CASES, ids=[c[0] for c in PY_CASES])
