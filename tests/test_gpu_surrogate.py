@@ -1,7 +1,11 @@
-"""Surrogate mechanics on the GPU: an ensemble trained (by the library's kernels) on a
-smooth function of the 6 inputs answers in-distribution queries accurately where its
-members agree, and its spread grows far outside the training range, which is what sends a
-query back to the simulation; and the batched-simulation outputs have the expected form."""
+"""Surrogate on the GPU: an ensemble trained (by the library's kernels) on a smooth
+function of the 6 inputs answers in-distribution queries accurately where its members
+agree, and its spread grows far outside the training range, which is what sends a query
+back to the simulation; the batched-simulation outputs have the expected form; and the
+surrogate of the ripple sweep, trained on batched PIC runs, meets the 5% output-power
+target wherever it answers and answers far faster than the simulation runs."""
+import os
+
 import numpy as np
 import pytest
 
@@ -22,43 +26,94 @@ def env():
 
 
 def _target(x):
-    """Smooth stand-in outputs: 32 log-energies and a frequency."""
+    """Smooth stand-in outputs: a 32-sample power envelope and a frequency."""
     s = np.linspace(0, 1, 32)
     amp = 1.0 + 0.5 * x[:, :1] + 0.3 * x[:, 1:2] * x[:, 2:3]
-    env = -3.0 + amp * s + 0.2 * np.sin(np.pi * (x[:, 3:4] + s)) + 0.1 * x[:, 4:5] * x[:, 5:6]
+    env = 0.5 + amp * s + 0.2 * np.sin(np.pi * (x[:, 3:4] + s)) + 0.1 * x[:, 4:5] * x[:, 5:6]
     freq = 10.0 + 2.0 * x[:, 5:6]
     return np.concatenate([env, freq], 1)
 
 
 def test_ensemble_answers_in_range_and_flags_extrapolation(env):
+    """The answer gate is calibrated on validation queries (the largest member spread under
+    which every validation error stays below 4%); held-out in-range queries it answers are
+    within 5%, and far outside the training range the spread grows and it answers fewer."""
     pic, S = env
     rng = np.random.default_rng(31)
     X = rng.uniform(-1, 1, (2048, 6))
     ens = S.Ensemble(5, S.SIZES, max_batch=256, seed=32)
     ens.fit(X, _target(X), steps=3000, batch=128, lr=1e-3, seed=33)
-    Xin = rng.uniform(-0.9, 0.9, (256, 6))
-    mean, ok, spread_in = ens.answer(Xin, tol=0.05)
-    P = S.Ensemble.power(_target(Xin))
-    err = np.abs(S.Ensemble.power(mean) - P) / P
+
+    def errors(Xq):
+        mean, _, spread = ens.answer(Xq)
+        P = S.Ensemble.power(_target(Xq))
+        return spread, np.abs(S.Ensemble.power(mean) - P) / np.abs(P)
+
+    sv, ev = errors(rng.uniform(-0.9, 0.9, (256, 6)))
+    tau = S.Ensemble.calibrate(sv, ev, target=0.05, margin=0.8)
+    spread_in, err = errors(rng.uniform(-0.9, 0.9, (256, 6)))
+    ok = spread_in <= tau
     assert ok.mean() >= 0.5
-    assert np.median(err[ok]) <= 0.05
-    Xout = rng.uniform(2.5, 3.5, (256, 6))
-    _, ok_out, spread_out = ens.answer(Xout, tol=0.05)
+    assert err[ok].max() <= 0.05
+    spread_out, _ = errors(rng.uniform(2.5, 3.5, (256, 6)))
     assert np.median(spread_out) > 3 * np.median(spread_in)
-    assert ok_out.mean() < ok.mean()
+    assert (spread_out <= tau).mean() < ok.mean()
 
 
 def test_batch_outputs_of_two_small_instances(env):
+    """Two instances as one union, 1024 steps: the recorded port power has the run's
+    shape, is zero until the fields of the beam reach the output plane (about 1.5 cm of
+    output guide at c: ~500 steps), and present by the end of the run."""
     pic, S = env
-    from workloads.sweep import sweep_instance, WEIGHT, R0
-    ins = []
-    for i in (0, 1):
-        x = sweep_instance(i, scale=0.002, mesh_scale=0.1)
-        x["out_z"] = x["sws"][0]
-        x["probe"] = (x["sws"][0] + 1.5 * x["params"]["period"], 0.7 * (R0 - x["params"]["depth"]))
-        ins.append(x)
-    env_, freq = S.batch_outputs(ins, 1.0e-13, 2.5, 256, 8, QE, ME, WEIGHT, EPS0, MU0, C0)
-    assert env_.shape == (2, 32) and freq.shape == (2,)
+    from workloads.sweep import sweep_instance, WEIGHT
+    ins = [sweep_instance(i, scale=0.002, mesh_scale=0.1) for i in (0, 1)]
+    steps, every, dt = 1024, 8, 1.0e-13
+    env_, freq, P = S.batch_outputs(ins, dt, 2.5, steps, every, QE, ME, WEIGHT, EPS0, MU0, C0)
+    assert env_.shape == (2, 32) and freq.shape == (2,) and P.shape == (2, steps // every)
     assert np.all(np.isfinite(env_)) and np.all(freq > 0)
-    # the beam's field builds up from zero: energy grows over the run
-    assert np.all(env_[:, -1] > env_[:, 0])
+    first = int(0.5 * 1.5e-2 / (C0 * dt * every))      # well before the fields arrive
+    assert np.all(np.abs(P[:, :first]) <= 1e-6 * np.abs(P).max())
+    assert np.all(np.abs(P[:, -P.shape[1] // 8:]).max(1) > 1e-3 * np.abs(P).max())
+
+
+def test_sweep_surrogate_meets_the_power_target_where_it_answers_and_gains(env):
+    """The sweep's surrogate as the benchmark builds it (``surrogate.study``): 1024 training,
+    128 validation and 128 held-out PIC runs of reduced instances (16384 steps, 5% of the
+    particles, 450 triangles per cm^2), 64 to a union; 5 members trained on the GPU; the
+    gate calibrated on the validation runs.  Held out: it answers at least 80% of the runs
+    and every answer is within 5% of the simulated arrival power.  Gain: an answer costs
+    at least 1e5 times less than a simulated run, so the gated surrogate (answers, and
+    simulations for the runs it does not answer) costs the simulations it falls back on
+    and little more: at least 1 / (1 - answered) / 1.01 times less than simulating all."""
+    pic, S = env
+    import multiprocessing as mp
+    import torch
+    from workloads.sweep import WEIGHT, SURROGATE_SCALE, surrogate_instance
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+    try:
+        r = S.study(surrogate_instance, 1024, 128, 128, 16384, 8, 1.0e-13, QE, ME, WEIGHT,
+                    EPS0, MU0, C0, scale=SURROGATE_SCALE, pool=pool)
+    finally:
+        pool.close()
+    ok, err = r["answered"], r["power_err"]
+    assert ok.mean() >= 0.8, ok.mean()
+    assert err[ok].max() <= 0.05, err[ok].max()
+    assert np.median(r["freq_err"][ok]) <= 0.25
+    # answers per second: every member on 65536 queries, timed on the device
+    ens = r["ensemble"]
+    q = torch.tensor(np.random.default_rng(5).uniform(-1, 1, (65536, 6)), dtype=torch.float32,
+                     device="cuda")
+    Yq = torch.empty((ens.members, 65536, S.N_OUT), dtype=torch.float32, device="cuda")
+    pic.pic_mlp_forward(ens.net, q, tensor_cores=True, out=Yq)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        pic.pic_mlp_forward(ens.net, q, tensor_cores=True, out=Yq)
+    e1.record()
+    torch.cuda.synchronize()
+    s_query = e0.elapsed_time(e1) * 1e-3 / (5 * 65536)
+    s_run = r["sim_seconds"] / r["runs"]
+    assert s_run / s_query >= 1e5, (s_run, s_query)
+    f = ok.mean()
+    cost = (1.0 - f) + s_query / s_run        # every query answered or sent back, per run
+    assert cost <= 1.01 * (1.0 - f) + 1e-4, cost

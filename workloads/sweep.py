@@ -51,11 +51,20 @@ def sweep_particles(i, scale=1.0):
     return max(1, int(round(n * scale)))
 
 
-def sweep_instance(i, scale=1.0, mesh_scale=1.0):
+def sweep_instance(i, scale=1.0, mesh_scale=1.0, tri_per_cm2=None):
     """Mesh and beam of instance i.  ``scale`` multiplies the particle count and
-    ``mesh_scale`` the triangle count (tests and surrogate data use fractions of them)."""
+    ``mesh_scale`` the triangle count (tests and surrogate data use fractions of them);
+    ``tri_per_cm2``, if given, sets the triangle count from the meridian area instead, so
+    that every instance has the same mesh spacing (the surrogate's data: the drawn count
+    would otherwise be a hidden input)."""
     p = sweep_params(i)
     n_tri = max(2000, int(p["n_tri"] * mesh_scale))
+    if tri_per_cm2 is not None:
+        R, z_end, _ = bwo_wall(r0=R0, ripple=p["depth"], period=p["period"],
+                               n_periods=p["n_periods"], guide=GUIDE)
+        zz = np.linspace(0.0, z_end, 20001)
+        area_cm2 = float(np.trapezoid(R(zz), zz)) * 1e4
+        n_tri = max(2000, int(round(tri_per_cm2 * area_cm2)))
     # deep, short ripples on a coarse mesh need the wall sampled more finely to conform
     for refine in (1.0, 0.7, 0.5, 0.35):
         try:
@@ -74,6 +83,17 @@ def sweep_instance(i, scale=1.0, mesh_scale=1.0):
     rb = 0.7 * (R0 - p["depth"])
     z, r, ur, up, uz = bwo_beam(n, r_in=rb - 0.05e-2, r_out=rb + 0.05e-2, z0=zs0, z1=zs1,
                                 voltage=p["voltage"], seed=4000 + i)
-    return dict(params=p, nodes=nodes, tris=tris, be=be, bt=bt, z_end=z_end, z=z, r=r, ur=ur,
-                up=up, uz=uz, n=n, sws=(zs0, zs1), vz=vz,
+    return dict(params=p, nodes=nodes, tris=tris, be=be, bt=bt, z_end=z_end, r_out=R0, z=z, r=r,
+                ur=ur, up=up, uz=uz, n=n, sws=(zs0, zs1), vz=vz,
                 current_eff=n * QE * WEIGHT * vz / (zs1 - zs0))
+
+
+SURROGATE_SCALE = 0.05
+SURROGATE_TRI_PER_CM2 = 450.0
+
+
+def surrogate_instance(i):
+    """Instance i as the surrogate's data takes it: 450 triangles per cm^2 of the meridian
+    plane (the same spacing, ~0.7 mm, for every instance) and SURROGATE_SCALE of its
+    particles."""
+    return sweep_instance(i, scale=SURROGATE_SCALE, tri_per_cm2=SURROGATE_TRI_PER_CM2)
