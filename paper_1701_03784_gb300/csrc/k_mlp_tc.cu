@@ -7,13 +7,17 @@
 //  * the activations of each tile (128 x K) sit in shared memory in the no-swizzle
 //    K-major layout (8 x 8 core matrices of 16-byte rows, K-adjacent core matrices 128
 //    bytes apart, 8-row groups K/8 x 128 bytes apart); the layer's weights stream through
-//    a buffer of 128 output rows (a 128-row slice of the packed N x K weights is
-//    contiguous), loaded by a load warp as soon as the products that read the buffer have
-//    completed;
-//  * one thread of the control warp issues tcgen05.mma (kind::f16, M = 128, N = the rows of
-//    the slice, 16 of K at a time) into the tile's 128 x 256 FP32 accumulator in TMEM (the
-//    two accumulators fill TMEM's 512 columns), releasing each weight buffer with a
-//    commit and signalling the tile's epilogue with another after its last slice;
+//    a 64 KB buffer in chunks of all its output rows (at most 256) by 128 of K, each one
+//    contiguous run of the packed weights (chunk_off) brought by one bulk copy from the
+//    load warp as soon as the products that read the buffer have completed;
+//  * one thread of the control warp issues tcgen05.mma (kind::f16, M = 128, N = the layer's
+//    width, 16 of K at a time) for both tiles on each chunk (the weights are read from L2
+//    once per block) into the tile's 128 x 256 FP32 accumulator in TMEM (the two
+//    accumulators fill TMEM's 512 columns), releasing the weight buffer with a commit and
+//    signalling the tile's epilogue with another after its layer's last chunk.  Products
+//    of the full width read each operand row once per layer and ask less shared-memory
+//    bandwidth per flop than narrower ones (measured: N = 128 products, or chunks of 64 or
+//    32 of K in a deeper ring, ran 4% to 17% slower);
 //  * eight warps per tile (two per TMEM lane quadrant, each half the columns) read the
 //    accumulator with tcgen05.ld, add the bias, apply the tanh-GELU (hidden layers) and
 //    write the next layer's BF16 operand back into the tile, or write the FP32 outputs,
@@ -39,16 +43,16 @@ constexpr int LOAD_WARP = CTRL_WARP + 1;       // lane 0 streams the weights
 constexpr int NTH = (LOAD_WARP + 1) * 32;
 constexpr int KMAX = 256;
 constexpr int NMAX = 256;
-constexpr int WROWS = 128;    // output rows per weight slice (N of each product)
-constexpr int NBUF = 1;       // weight buffers (two tiles' products hide a slice's load)
+constexpr int WROWS = 256;    // output rows per weight chunk (N of each product)
+constexpr int WK = 128;       // K columns per weight chunk
+constexpr int NBUF = 1;       // weight buffers
 constexpr int TMEM_COLS = 512;
 constexpr int BIAS_MAX = MLP_MAX_LAYERS * NMAX;
 constexpr long long WAIT_LIMIT = 1LL << 22;
-constexpr float C_GELU = 0.7978845608028654f;   // sqrt(2/pi)
 
 struct PingSmem {
     uint16_t a[NTILE][TM * KMAX];        // activations of each tile, core-matrix layout
-    uint16_t w[NBUF][WROWS * KMAX];      // weight buffer(s) of 128 output rows
+    uint16_t w[NBUF][WROWS * WK];        // weight chunks: 128 output rows x 128 of K
     alignas(16) float bias[BIAS_MAX];    // every layer's bias of the member (bmember used)
     unsigned long long wfull[NBUF];      // a weight buffer landed
     unsigned long long wempty[NBUF];     // the products that read a weight buffer completed
@@ -63,6 +67,17 @@ static_assert(offsetof(PingSmem, w) % 1024 == 0 && offsetof(PingSmem, bias) % 16
 // element offset of (row r, column k) in a core-matrix tile with kp (padded) columns
 __host__ __device__ __forceinline__ int core_off(int r, int k, int kp) {
     return ((r >> 3) * (kp >> 3) * 64) + ((k >> 3) * 64) + ((r & 7) * 8) + (k & 7);
+}
+
+// element offset of weight (row r, column k) of a layer's packed np x kp weights: chunk
+// (q, kc) = rows [128 q, ...) x columns [128 kc, ...) is one contiguous run (the rows of
+// every earlier row slice, then this slice's earlier K chunks), in core-matrix layout
+// with its own width, so that one bulk copy brings a chunk into shared memory
+__host__ __device__ __forceinline__ long long chunk_off(int r, int k, int kp, int np) {
+    const int q = r / WROWS, kc = k / WK;
+    const int rows = min(WROWS, np - q * WROWS), kw = min(WK, kp - kc * WK);
+    return (long long)q * WROWS * kp + (long long)rows * kc * WK +
+           core_off(r - q * WROWS, k - kc * WK, kw);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -147,13 +162,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity
     return false;
 }
 
-// tanh-GELU with the hardware tanh approximation (relative error about 2^-11, below the
-// BF16 rounding of the result)
-__device__ __forceinline__ float gelu_approx(float z) {
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(C_GELU * (z + 0.044715f * z * z * z)));
-    return 0.5f * z * (1.f + t);
-}
 // 1-D bulk copy global -> shared completing on an mbarrier (16-byte aligned, size % 16 == 0)
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
                                           unsigned long long *bar) {
@@ -178,8 +186,8 @@ __device__ __forceinline__ uint4 pack8x2(const float *v) {
     return q;
 }
 
-// Packed pairs of FP32 (element 0 in the low half): the epilogue's arithmetic runs two
-// columns per instruction on the FP32 pipes, and tanh two per instruction in FP16.
+// Packed pairs of FP32 (element 0 in the low half): the bias is added two columns per
+// instruction on the FP32 pipes.
 __device__ __forceinline__ unsigned long long f2(float a, float b) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
@@ -193,48 +201,41 @@ __device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigne
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
-                                                   unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 // tanh-GELU of a pair, returned as two BF16 (element 0 low): 0.5 z (1 + tanh(w)),
-// w = sqrt(2/pi) (z + 0.044715 z^3).  tanh is the hardware approximation on FP16 pairs
-// (absolute error about 2^-10.7, below the BF16 rounding of the result); the argument is
-// converted with saturation, so a huge |w| gives tanh = +-1.
+// w = z (c0 + c1 z^2), c0 = sqrt(2/pi), c1 = 0.044715 sqrt(2/pi).  z is rounded to BF16
+// once and the rest runs on BF16 pairs (the hardware tanh approximation included): the
+// result is the next layer's BF16 operand, and the BF16 steps add about one rounding of
+// it (relative 2^-8) to the one it takes anyway.
 __device__ __forceinline__ unsigned gelu2_bf16(unsigned long long z) {
-    const unsigned long long k3 = f2(0.044715f, 0.044715f), one = f2(1.f, 1.f);
-    const unsigned long long kc = f2(C_GELU, C_GELU), half = f2(0.5f, 0.5f);
-    const unsigned long long w = mul2(mul2(z, kc), fma2(mul2(z, z), k3, one));
-    float w0, w1;
-    f2_split(w, w0, w1);
-    unsigned hw, ht;
-    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(hw) : "f"(w1), "f"(w0));
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(ht) : "r"(hw));
-    const __half2 th = *reinterpret_cast<const __half2 *>(&ht);
-    const float2 t = __half22float2(th);
-    const unsigned long long hz = mul2(z, half);
-    float r0, r1;
-    f2_split(fma2(hz, f2(t.x, t.y), hz), r0, r1);
-    return bf16x2_bits(r0, r1);
+    float z0, z1;
+    f2_split(z, z0, z1);
+    unsigned zb, u, q, w, t, h, y;
+    const unsigned c1 = 0x3D123D12u;   // BF16 pair of 0.044715 sqrt(2/pi) = 0.035677
+    const unsigned c0 = 0x3F4C3F4Cu;   // BF16 pair of sqrt(2/pi) = 0.79788
+    const unsigned half = 0x3F003F00u; // BF16 pair of 0.5
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(zb) : "f"(z1), "f"(z0));
+    asm("mul.rn.bf16x2 %0, %1, %1;" : "=r"(u) : "r"(zb));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(q) : "r"(u), "r"(c1), "r"(c0));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(w) : "r"(zb), "r"(q));
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(w));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(zb), "r"(half));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(y) : "r"(h), "r"(t), "r"(h));
+    return y;
 }
 
 // bias, GELU and BF16 of 16 accumulator columns c .. c+15 of row erow, written as the
 // next layer's operand (core-matrix layout, np columns)
 __device__ __forceinline__ void gelu_chunk(const unsigned (&r)[16], const float *bias, int c,
                                            uint16_t *act, int erow, int np) {
-    const unsigned long long *bias2 = reinterpret_cast<const unsigned long long *>(bias + c);
+    const ulonglong2 *bias4 = reinterpret_cast<const ulonglong2 *>(bias + c);
     unsigned p[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++)
-        p[j] = gelu2_bf16(add2(f2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])),
-                               bias2[j]));
+    for (int j = 0; j < 4; j++) {
+        const ulonglong2 b = bias4[j];
+        p[2 * j] = gelu2_bf16(add2(f2(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1])), b.x));
+        p[2 * j + 1] = gelu2_bf16(
+            add2(f2(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])), b.y));
+    }
     *reinterpret_cast<uint4 *>(act + core_off(erow, c, np)) = make_uint4(p[0], p[1], p[2], p[3]);
     *reinterpret_cast<uint4 *>(act + core_off(erow, c + 8, np)) = make_uint4(p[4], p[5], p[6], p[7]);
 }
@@ -243,15 +244,21 @@ __device__ __forceinline__ void arrive(unsigned long long *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
-// The weight slices in the order the products use them: layer by layer, slice q = rows
-// [64q, 64q + 64) of the layer's packed N x K weights; both tiles' products read a slice
-// before the next one is needed, so each slice is loaded once per block.
-struct SliceIter {
-    int l = 0, q = 0;
+// The weight chunks in the order the products use them: layer by layer, row slice q
+// (output rows [128 q, 128 q + 128)), K chunk kc (columns [128 kc, 128 kc + 128)); both
+// tiles' products read a chunk before the next one is needed, so each chunk is loaded
+// once per block.
+struct ChunkIter {
+    int l = 0, q = 0, kc = 0;
     __device__ __forceinline__ bool next(const MlpTc &tc) {
+        if (++kc * WK < tc.kp[l]) return true;
+        kc = 0;
         if (++q * WROWS < tc.np[l]) return true;
         q = 0;
         return ++l < tc.L;
+    }
+    __device__ __forceinline__ bool last_of_layer(const MlpTc &tc) const {
+        return (q + 1) * WROWS >= tc.np[l] && (kc + 1) * WK >= tc.kp[l];
     }
 };
 
@@ -296,11 +303,11 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          ::"r"(smem_u32(&sm.bbar)), "r"(bb) : "memory");
             bulk_load(sm.bias, tc.b + (long long)z * tc.bmember, bb, &sm.bbar);
-            SliceIter it;
+            ChunkIter it;
             long long c = 0;
             do {
                 const int b = (int)(c % NBUF);
-                // the products that read this buffer NBUF slices ago have completed
+                // the products that read this buffer NBUF chunks ago have completed
                 if (c >= NBUF &&
                     !mbar_wait(&sm.wempty[b], (unsigned)(((c - NBUF) / NBUF) & 1), polls)) {
                     ok = false;
@@ -308,15 +315,14 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
                 }
                 const int kp = tc.kp[it.l];
                 const int rows = min(WROWS, tc.np[it.l] - it.q * WROWS);
-                const unsigned wb = (unsigned)(rows * kp * 2);
+                const int kw = min(WK, kp - it.kc * WK);
+                const unsigned wb = (unsigned)(rows * kw * 2);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                              ::"r"(smem_u32(&sm.wfull[b])), "r"(wb) : "memory");
-                // in copies of 16 rows (8-row groups are contiguous), all in flight at once
+                // the chunk is one contiguous run of the packed weights (chunk_off)
                 const uint16_t *src = tc.w + (long long)z * tc.wmember + tc.woff[it.l] +
-                                      (long long)it.q * WROWS * kp;
-                for (int r0 = 0; r0 < rows; r0 += 16)
-                    bulk_load(sm.w[b] + r0 * kp, src + (long long)r0 * kp,
-                              (unsigned)(16 * kp * 2), &sm.wfull[b]);
+                                      chunk_off(it.q * WROWS, it.kc * WK, kp, tc.np[it.l]);
+                bulk_load(sm.w[b], src, wb, &sm.wfull[b]);
                 c++;
             } while (it.next(tc));
             // before the block exits, every copy issued here has landed
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
     } else if (warp == CTRL_WARP) {
         // ---- products --------------------------------------------------------------------
         if (lane == 0) {
-            SliceIter it;
+            ChunkIter it;
             long long c = 0;
             bool first = true;
             do {
@@ -339,24 +345,27 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
                     break;
                 }
                 const int rows = min(WROWS, tc.np[l] - it.q * WROWS);
-                const bool last_slice = (it.q + 1) * WROWS >= tc.np[l];
+                const int kw = min(WK, kp - it.kc * WK);
+                const bool last_chunk = it.last_of_layer(tc);
                 const unsigned w0 = smem_u32(sm.w[b]);
-                const unsigned sbo = (unsigned)kp / 8u * 128u;
+                const unsigned sbo_a = (unsigned)kp / 8u * 128u;
+                const unsigned sbo_w = (unsigned)kw / 8u * 128u;
                 const unsigned id = idesc_bf16(rows);
                 for (int t = 0; t < NTILE && ok; t++) {
-                    // a tile's first slice of a layer waits for its operand (and for its
+                    // a tile's first chunk of a layer waits for its operand (and for its
                     // accumulator to have been read)
-                    if (it.q == 0 && !mbar_wait(&sm.ready[t], (unsigned)(l & 1), polls)) {
+                    if (it.q == 0 && it.kc == 0 &&
+                        !mbar_wait(&sm.ready[t], (unsigned)(l & 1), polls)) {
                         ok = false;
                         break;
                     }
                     fence_after();
-                    const unsigned a0 = smem_u32(sm.a[t]);
+                    const unsigned a0 = smem_u32(sm.a[t]) + (unsigned)(it.kc * (WK / 16)) * 256u;
                     const unsigned d = tmem + (unsigned)(t * 256 + it.q * WROWS);
-                    for (int kk = 0; kk < kp / 16; kk++)
-                        mma_bf16(d, sdesc(a0 + kk * 256u, 128u, sbo),
-                                 sdesc(w0 + kk * 256u, 128u, sbo), id, kk > 0);
-                    if (last_slice) mma_commit(&sm.accdone[t]);
+                    for (int kk = 0; kk < kw / 16; kk++)
+                        mma_bf16(d, sdesc(a0 + kk * 256u, 128u, sbo_a),
+                                 sdesc(w0 + kk * 256u, 128u, sbo_w), id, it.kc > 0 || kk > 0);
+                    if (last_chunk) mma_commit(&sm.accdone[t]);
                     first = false;
                 }
                 if (!ok) break;
@@ -571,7 +580,7 @@ __global__ void k_mlp_pack(MlpTc tc, const float *params, long long P, PackArgs 
     uint16_t *dst = tc.w + (long long)z * tc.wmember + tc.woff[l];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np * kp; i += gridDim.x * blockDim.x) {
         const int r = i / kp, c = i % kp;
-        dst[core_off(r, c, kp)] = bf16_bits(r < nn && c < k ? W[(long long)r * k + c] : 0.f);
+        dst[chunk_off(r, c, kp, np)] = bf16_bits(r < nn && c < k ? W[(long long)r * k + c] : 0.f);
     }
     const float *b = params + (long long)z * P + pa.boff[l];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
