@@ -481,6 +481,15 @@ pic_status pic_mlp_forward(pic_mlp *m, const float *X, float *Y, int64_t n, int3
  * wider than 256 in N or K stay on CUDA cores.  A bounded tensor-core wait that gives up
  * makes the call that ran it return PIC_ERR_TIMEOUT.  Errors: ARG (a width above 256). */
 pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores);
+/* Bound of the tensor-core inference kernel's waits (pic_mlp_forward with tensor_cores):
+ * the number of polls, each suspending the waiting thread for at most a system-set time,
+ * that a wait for a weight chunk, a product or a tile's operand makes before it gives up.
+ * Default 4194304.  A block whose wait gives up stops, waits with the default bound for
+ * its own copies and products still in flight, frees its tensor memory and exits; the
+ * forward call then returns PIC_ERR_TIMEOUT and its outputs are undefined.  Not an
+ * operation of the paper: it lets a caller (a test) make the waits run out, with 0 polls.
+ * The training products keep the default bound.  Errors: ARG (negative count). */
+pic_status pic_mlp_set_wait_limit(pic_mlp *m, int64_t polls);
 void pic_mlp_destroy(pic_mlp *m);
 
 /* Release a simulation (its device memory included) or a mesh; NULL is ignored.  A mesh

@@ -46,7 +46,9 @@ constexpr int NMAX = 256;
 constexpr int WROWS = 256;    // output rows per weight chunk (N of each product)
 constexpr int WK = 128;       // K columns per weight chunk
 constexpr int NBUF = 1;       // weight buffers
-constexpr int TMEM_COLS = 512;
+constexpr int TMEM_COLS = 512;    // training products
+constexpr int MIN_BLOCKS = 1;     // inference blocks resident per SM
+constexpr int INF_TMEM = NTILE * 256;   // inference accumulators: 256 columns a tile
 constexpr int BIAS_MAX = MLP_MAX_LAYERS * NMAX;
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
@@ -262,7 +264,7 @@ struct ChunkIter {
     }
 };
 
-__global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, float *Y,
+__global__ void __launch_bounds__(NTH, MIN_BLOCKS) k_mlp_tc(MlpTc tc, const float *X, float *Y,
                                                    long long n, long long row_base) {
     extern __shared__ unsigned char raw[];
     const unsigned pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&sm.tmem)), "r"(TMEM_COLS) : "memory");
+                     ::"r"(smem_u32(&sm.tmem)), "r"(INF_TMEM) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mlp_tc(MlpTc tc, const float *X, flo
     fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS) : "memory");
+                     "r"(INF_TMEM) : "memory");
 }
 
 // ---- products of the training path ----
@@ -636,6 +638,8 @@ pic_status mlp_tc_forward(const MlpTc &tc, const float *X, float *Y, int64_t n, 
     }
     const int smem = (int)sizeof(PingSmem) + 1024;
     PIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
     PIC_CUDA_TRY(cudaMemsetAsync(tc.err, 0, sizeof(unsigned int), s));
     // grid: members along x, pairs of tiles along y (at most 65535 pairs per launch)
     const long long pairs = (n + NTILE * TM - 1) / (NTILE * TM);

@@ -552,4 +552,15 @@ extern "C" pic_status pic_mlp_set_training(pic_mlp *m, int32_t tensor_cores) try
 }
 PIC_CATCH("pic_mlp_set_training")
 
+extern "C" pic_status pic_mlp_set_wait_limit(pic_mlp *m, int64_t polls) try {
+    MLP_CHECK(m, "pic_mlp_set_wait_limit");
+    if (polls < 0) {
+        set_error("pic_mlp_set_wait_limit: negative poll count");
+        return PIC_ERR_ARG;
+    }
+    m->impl->tc.wait_polls = polls;
+    return PIC_OK;
+}
+PIC_CATCH("pic_mlp_set_wait_limit")
+
 extern "C" void pic_mlp_destroy(pic_mlp *m) { delete m; }

@@ -93,6 +93,7 @@ _SIGS = {
     "pic_mlp_grad": [_P, _P, _P, _I64, _P, _P, _P],
     "pic_mlp_forward": [_P, _P, _P, _I64, _I32, _P],
     "pic_mlp_set_training": [_P, _I32],
+    "pic_mlp_set_wait_limit": [_P, _I64],
     "pic_fields_set": [_P, _P, _P, _P],
     "pic_particles_inject": [_P, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _P],
     "pic_step": [_P, _I64, _P],
@@ -649,6 +650,11 @@ def pic_mlp_grad(m, X, T, stream=None):
     _check(_lib.pic_mlp_grad(m.ptr, _dev(X, "X"), _dev(T, "T"), X.shape[0], _ptr(g), _ptr(loss),
                              _stream(stream)), "pic_mlp_grad")
     return g, loss
+
+
+def pic_mlp_set_wait_limit(m, polls):
+    """Polls before a wait of the tensor-core inference kernel gives up (default 4194304)."""
+    _check(_lib.pic_mlp_set_wait_limit(m.ptr, int(polls)), "pic_mlp_set_wait_limit")
 
 
 def pic_mlp_set_training(m, tensor_cores):

@@ -2,7 +2,8 @@
 waits on mbarriers with a poll limit; a test sets the limit to 0 polls so that every
 such wait gives up at once.  The step must then end (no hang), the next diagnostics and
 charge read-backs must report PIC_ERR_TIMEOUT, and the context must stay usable: a new
-simulation afterwards steps exactly like one run before the timeout."""
+simulation afterwards steps exactly like one run before the timeout.  The surrogate
+network's tensor-core inference kernel waits the same way, under its own limit."""
 import numpy as np
 import pytest
 
@@ -75,3 +76,28 @@ def test_waits_that_run_out_are_reported_and_leave_the_context_usable(pic):
     for k in ("E", "B", "J"):
         assert np.array_equal(d[k], d_ref[k]), k
     assert d["dce_nonzero"] == 0
+
+
+def test_inference_waits_that_run_out_are_reported(pic):
+    """The tensor-core inference kernel's waits (weight chunks, products, operands) with a
+    limit of 0 polls: the forward call returns PIC_ERR_TIMEOUT instead of hanging, and with
+    the default bound restored the same network gives the same outputs bit for bit."""
+    import torch
+    from tests.mlp_util import flat, members
+    sizes, E = (6, 256, 256, 33), 3
+    m = pic.pic_mlp_create(E, sizes, 256)
+    pic.pic_mlp_params_set(m, np.stack([flat(W, b) for W, b in members(E, sizes, seed=41)]))
+    X = torch.tensor(np.random.default_rng(42).uniform(-1, 1, (1000, 6)), dtype=torch.float32,
+                     device="cuda")
+    Y0 = pic.pic_mlp_forward(m, X, tensor_cores=True).cpu().numpy()
+    pic.pic_mlp_set_wait_limit(m, 0)
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_mlp_forward(m, X, tensor_cores=True)
+    assert e.value.status == pic.PIC_ERR_TIMEOUT
+    assert "timed out" in pic.pic_last_error()
+    with pytest.raises(pic.PicError):
+        pic.pic_mlp_set_wait_limit(m, -1)
+    pic.pic_mlp_set_wait_limit(m, 1 << 22)
+    Y1 = pic.pic_mlp_forward(m, X, tensor_cores=True).cpu().numpy()
+    assert np.array_equal(Y0, Y1)
+    assert np.all(np.isfinite(pic.pic_mlp_forward(m, X, tensor_cores=False).cpu().numpy()))
