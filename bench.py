@@ -508,7 +508,7 @@ def run_surrogate(args):
         "inference_ms_65536": times, "roofline": {"bound": "tensor", "achieved": tf, "peak": peak,
                                                   "unit": "TFLOP/s", "frac": tf / peak if peak else None,
                                                   "flop_per_launch": flop},
-        "gate": {"spread_threshold": tau, "rule": "largest member spread (std/|mean| of the mean "
+        "gate": {"spread_threshold": tau, "rule": "largest member spread (std/|mean| of the arrival "
                  "power) under which every validation error is below 4%"},
         "heldout": {"answered": float(ok.mean()),
                     "power_err_answered_max": float(et[ok].max()) if ok.any() else None,
