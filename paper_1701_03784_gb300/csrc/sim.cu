@@ -100,6 +100,16 @@ struct SimBase {
     int device = 0;
 };
 
+// live slots of each of nch ranges of `chunk` slots, from the device slot count *n (which a
+// re-sort may have lowered below the host's count)
+__global__ void k_chunk_counts(const int64_t *n, int64_t *out, int64_t chunk, int nch) {
+    const int c = threadIdx.x;
+    if (c < nch) {
+        const int64_t r = *n - (int64_t)c * chunk;
+        out[c] = r < 0 ? 0 : (r > chunk ? chunk : r);
+    }
+}
+
 template <class P>
 struct SimImpl final : SimBase {
     using R = typename P::R;
@@ -155,8 +165,10 @@ struct SimImpl final : SimBase {
 
     bool timing_on = false;
     // host round trips (step_host): uploads and downloads run on streams of their own,
-    // chunk by chunk
-    static constexpr int RT_CHUNKS = 8;
+    // chunk by chunk (16M slots, ms per step: 2, 3, 4, 6, 8, 16, 32 chunks -> 2.63, 2.53,
+    // 2.57, 2.66, 2.75, 3.15, 3.15; each chunk costs a particle-kernel launch and six
+    // copies each way, more than the shorter pipeline tail saves)
+    static constexpr int RT_CHUNKS = 3;
     // CUDA-graph replay of whole periods of steps (2 x the re-sort interval: the buffer
     // parities and the re-sort phase are back where they started)
     bool use_graph = false, stepped = false;
@@ -171,6 +183,8 @@ struct SimImpl final : SimBase {
     long long g_kernels = 0;   // kernels recorded in g_exec
     cudaStream_t rt_stream = nullptr, up_stream = nullptr;
     cudaEvent_t rt_chunk[RT_CHUNKS] = {}, rt_step = nullptr, rt_done = nullptr, rt_up = nullptr;
+    cudaEvent_t rt_upc[RT_CHUNKS] = {}, rt_pushc[RT_CHUNKS] = {};   // a chunk uploaded / pushed
+    int64_t *d_chunk_n = nullptr;                                    // live slots per chunk
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
 
@@ -181,6 +195,8 @@ struct SimImpl final : SimBase {
         if (g_stream) cudaStreamDestroy(g_stream);
         if (rt_stream) {
             for (auto e : rt_chunk) cudaEventDestroy(e);
+            for (auto e : rt_upc) cudaEventDestroy(e);
+            for (auto e : rt_pushc) cudaEventDestroy(e);
             cudaEventDestroy(rt_step);
             cudaEventDestroy(rt_done);
             cudaEventDestroy(rt_up);
@@ -985,59 +1001,82 @@ struct SimImpl final : SimBase {
         return PIC_OK;
     }
 
+    // the part of a step before the particle kernel: the Gauss-law reference of a new
+    // state, emission, the face kernel (B update, J / Q_abs cleared), probes and ports
+    pic_status step_begin(FieldArgs<P> &fa, cudaStream_t s) {
+        if (dgl_dirty) {
+            // DGL reference res = D_div D^n - Q^n before the first step of this state
+            PIC_CUDA_TRY(cudaMemsetAsync(Qwall, 0, sizeof(Acc) * m->N0, s));
+            launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, Qwall, D, dgl_ref, 1, E, B, mu_inv,
+                           parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
+            dgl_dirty = false;
+        }
+        if (emitting) {
+            EmitArgs<P> ea;
+            ea.line = eline;
+            ea.p = parts[cur];
+            ea.rec = rec;
+            ea.n_slots = d_n;
+            ea.counters = counters;
+            ea.Qn = Qn();
+            ea.Qwall = Qwall;
+            ea.cap = cap;
+            ea.per_step = em.per_step;
+            ea.rho0 = em.rho0;
+            ea.rho1 = em.rho1;
+            ea.u_normal = em.u_normal;
+            ea.u_thermal = em.u_thermal;
+            ea.seed = (unsigned long long)em.seed;
+            launch_emit<P>(ea, s);
+        }
+        // the face kernel clears J, Q_abs and (FP64) Q^{n+1}; in the FP32 build Q^{n+1} is
+        // written whole by the per-node update
+        fa.Qn = Qn();
+        fa.Qnext = Qbuf[1 - qcur];
+        launch_field_b<P>(fa, s);
+        if (probes_on) launch_probe<P>(probe, s);
+        if (ports_on) launch_port<P>(port, s);
+        return PIC_OK;
+    }
+
+    // the particle kernel's arguments for the slots `view` (the whole state, or a range of
+    // it), counted by the device value at `count`
+    PushArgs<P> push_args(const Particles<P> &view, const int64_t *count) const {
+        PushArgs<P> pa;
+        pa.rec = rec;
+        pa.p = view;
+        pa.n_slots = count;
+        pa.J = J;
+        pa.Q = Qbuf[1 - qcur];
+        pa.Qabs = Qabs;
+        pa.counters = counters;
+        pa.qmdt2 = (R)(0.5 * qm * dt);
+        pa.dt = (R)dt;
+        pa.inv_c2 = (R)(1.0 / (m->units.c * m->units.c));
+        pa.bz = (R)bz;
+        pa.walk_cap = m->units.walk_cap;
+        pa.ctas_per_sm = tune_ctas;
+        pa.pusher = pusher;
+        pa.wait_polls = wait_polls;
+        return pa;
+    }
+
+    // the part of a step after the particle kernel: the E update (edge residual, SpMV,
+    // node charge), the step count and, when due, the re-sort
+    void step_end(FieldArgs<P> &fa, cudaStream_t s) {
+        launch_field_e<P>(fa, s);
+        qcur = 1 - qcur;
+        n_steps++;
+        if (sort_interval > 0 && ++since_sort >= sort_interval) resort(s);
+    }
+
     pic_status step_direct(int64_t n, cudaStream_t s) {
         stepped = true;
         FieldArgs<P> fa = field_args();
         for (int64_t it = 0; it < n; it++) {
-            if (dgl_dirty) {
-                // DGL reference res = D_div D^n - Q^n before the first step of this state
-                PIC_CUDA_TRY(cudaMemsetAsync(Qwall, 0, sizeof(Acc) * m->N0, s));
-                launch_diag<P>(dd, J, Qn(), Qbuf[1 - qcur], Qabs, nullptr, Qwall, D, dgl_ref, 1, E, B, mu_inv,
-                               parts[cur], d_n, n_bound, q_scale(), 0.0, diag_out, s);
-                dgl_dirty = false;
-            }
-            if (emitting) {
-                EmitArgs<P> ea;
-                ea.line = eline;
-                ea.p = parts[cur];
-                ea.rec = rec;
-                ea.n_slots = d_n;
-                ea.counters = counters;
-                ea.Qn = Qn();
-                ea.Qwall = Qwall;
-                ea.cap = cap;
-                ea.per_step = em.per_step;
-                ea.rho0 = em.rho0;
-                ea.rho1 = em.rho1;
-                ea.u_normal = em.u_normal;
-                ea.u_thermal = em.u_thermal;
-                ea.seed = (unsigned long long)em.seed;
-                launch_emit<P>(ea, s);
-            }
-            Acc *Qnext = Qbuf[1 - qcur];
-            // the face kernel clears J, Q_abs and (FP64) Q^{n+1}; in the FP32 build Q^{n+1} is
-            // written whole by the per-node update
-            fa.Qn = Qn();
-            fa.Qnext = Qnext;
-            launch_field_b<P>(fa, s);
-            if (probes_on) launch_probe<P>(probe, s);
-            if (ports_on) launch_port<P>(port, s);
-            PushArgs<P> pa;
-            pa.rec = rec;
-            pa.p = parts[cur];
-            pa.n_slots = d_n;
-            pa.J = J;
-            pa.Q = Qnext;
-            pa.Qabs = Qabs;
-            pa.counters = counters;
-            pa.qmdt2 = (R)(0.5 * qm * dt);
-            pa.dt = (R)dt;
-            pa.inv_c2 = (R)(1.0 / (m->units.c * m->units.c));
-            pa.bz = (R)bz;
-            pa.walk_cap = m->units.walk_cap;
-            pa.ctas_per_sm = tune_ctas;
-            pa.pusher = pusher;
-            pa.wait_polls = wait_polls;
+            pic_status st = step_begin(fa, s);
+            if (st != PIC_OK) return st;
+            const PushArgs<P> pa = push_args(parts[cur], d_n);
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (timing_on) {
                 e0 = take_event();
@@ -1049,10 +1088,7 @@ struct SimImpl final : SimBase {
                 cudaEventRecord(e1, s);
                 ev_pending.push_back({e0, e1});
             }
-            launch_field_e<P>(fa, s);
-            qcur = 1 - qcur;
-            n_steps++;
-            if (sort_interval > 0 && ++since_sort >= sort_interval) resort(s);
+            step_end(fa, s);
         }
         PIC_CUDA_TRY(cudaGetLastError());
         return PIC_OK;
@@ -1344,6 +1380,58 @@ struct SimImpl final : SimBase {
         return PIC_OK;
     }
 
+    // one step of step_host with the particle kernel run chunk by chunk between the
+    // copies: chunk c is uploaded once the previous step's write-back of it is done,
+    // pushed once it has landed, and written back once it is pushed (or, on a re-sort
+    // step, once the re-sort is done)
+    pic_status step_host_pipelined(char *h, int64_t n, int64_t chunk, cudaStream_t s) {
+        pic_status st;
+        stepped = true;
+        FieldArgs<P> fa = field_args();
+        if ((st = step_begin(fa, s)) != PIC_OK) return st;
+        k_chunk_counts<<<1, 32, 0, s>>>(d_n, d_chunk_n, chunk, RT_CHUNKS);
+        PIC_LAUNCHED();
+        const bool resort_due = sort_interval > 0 && since_sort + 1 >= sort_interval;
+        for (int c = 0; c < RT_CHUNKS; c++) {
+            const int64_t c0 = std::min(n, c * chunk), c1 = std::min(n, c0 + chunk);
+            PIC_CUDA_TRY(cudaStreamWaitEvent(up_stream, rt_chunk[c], 0));
+            if (c1 > c0 && (st = copy_slots(h, n, c0, c1, true, up_stream)) != PIC_OK) return st;
+            PIC_CUDA_TRY(cudaEventRecord(rt_upc[c], up_stream));
+            PIC_CUDA_TRY(cudaStreamWaitEvent(s, rt_upc[c], 0));
+            if (c1 > c0) {
+                Particles<P> v = parts[cur];
+                v.tri += c0;
+                v.l0 += c0;
+                v.l1 += c0;
+                v.ur += c0;
+                v.up += c0;
+                v.uz += c0;
+                v.pid += c0;
+                launch_push<P>(push_args(v, d_chunk_n + c), c1 - c0, s);
+            }
+            if (!resort_due) {
+                PIC_CUDA_TRY(cudaEventRecord(rt_pushc[c], s));
+                PIC_CUDA_TRY(cudaStreamWaitEvent(rt_stream, rt_pushc[c], 0));
+                if (c1 > c0 && (st = copy_slots(h, n, c0, c1, false, rt_stream)) != PIC_OK)
+                    return st;
+                PIC_CUDA_TRY(cudaEventRecord(rt_chunk[c], rt_stream));
+            }
+        }
+        step_end(fa, s);
+        if (resort_due) {
+            PIC_CUDA_TRY(cudaEventRecord(rt_step, s));
+            PIC_CUDA_TRY(cudaStreamWaitEvent(rt_stream, rt_step, 0));
+            for (int c = 0; c < RT_CHUNKS; c++) {
+                const int64_t c0 = std::min(n, c * chunk), c1 = std::min(n, c0 + chunk);
+                if (c1 > c0 && (st = copy_slots(h, n, c0, c1, false, rt_stream)) != PIC_OK)
+                    return st;
+                PIC_CUDA_TRY(cudaEventRecord(rt_chunk[c], rt_stream));
+            }
+        }
+        PIC_CUDA_TRY(cudaGetLastError());
+        return PIC_OK;
+    }
+
     pic_status step_host(void *state, int64_t n, int64_t steps, cudaStream_t s) override {
         if (!state || n < 0 || n > cap || steps < 0) {
             set_error("pic_step_host: bad argument");
@@ -1358,16 +1446,31 @@ struct SimImpl final : SimBase {
             PIC_CUDA_TRY(cudaStreamCreateWithFlags(&up_stream, cudaStreamNonBlocking));
             PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_up, cudaEventDisableTiming));
             for (auto &e : rt_chunk) PIC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            for (auto &e : rt_upc) PIC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            for (auto &e : rt_pushc) PIC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_step, cudaEventDisableTiming));
             PIC_CUDA_TRY(cudaEventCreateWithFlags(&rt_done, cudaEventDisableTiming));
         }
         char *h = static_cast<char *>(state);
-        const int64_t chunk = (n + RT_CHUNKS - 1) / RT_CHUNKS;
+        // chunks of whole particle-kernel tiles (512 slots), so that a chunk's tiles read
+        // none of the next chunk's slots
+        const int64_t chunk = ((n + RT_CHUNKS - 1) / RT_CHUNKS + 511) / 512 * 512;
+        // FP32 build (without kernel timing): after the first step each chunk is pushed as
+        // soon as it has landed and written back as soon as it is pushed, so the step's
+        // particle work overlaps both copy directions; the E update and any re-sort follow
+        // the last chunk (a re-sort moves slots between chunks: then the write-back waits
+        // for it)
+        const bool pipe = P::fixed && !timing_on;
         pic_status st;
+        if (pipe && !d_chunk_n && (st = dalloc(d_chunk_n, RT_CHUNKS)) != PIC_OK) return st;
         // uploads on their own stream, after the caller's earlier work
         PIC_CUDA_TRY(cudaEventRecord(rt_up, s));
         PIC_CUDA_TRY(cudaStreamWaitEvent(up_stream, rt_up, 0));
         for (int64_t k = 0; k < steps; k++) {
+            if (k > 0 && pipe) {
+                if ((st = step_host_pipelined(h, n, chunk, s)) != PIC_OK) return st;
+                continue;
+            }
             // upload; chunk c waits only for the previous step's download of chunk c, so the
             // two copy directions overlap
             for (int c = 0; c < RT_CHUNKS; c++) {
