@@ -416,9 +416,13 @@ pic_status pic_particles_raw_set(pic_sim *s, const void *host_src, int64_t n_slo
 /* n_steps steps of Sec. 3's cycle for a particle state that lives in page-locked host
  * memory between steps (raw layout above, n_slots slots, n_slots at most the capacity):
  * every step uploads it, steps, and writes it back.  Slots beyond the live count after a
- * re-sort removed particles are unspecified on return.  The download of one step runs on
- * an internal stream and overlaps, chunk by chunk, the upload of the next; the call is
- * asynchronous on cuda_stream, which waits for the last download.  Errors: PIC_ERR_ARG
+ * re-sort removed particles are unspecified on return.  Uploads and downloads run on
+ * internal streams, chunk by chunk: the download of one step overlaps the upload of the
+ * next, and (FP32 build, kernel timing off) after the first step the particle kernel runs
+ * on each chunk as soon as it has landed and each chunk is written back as soon as it is
+ * pushed (after the re-sort, on a re-sort step); the result is bit-identical to stepping
+ * on the device.  The call is asynchronous on cuda_stream, which waits for the last
+ * download.  Errors: PIC_ERR_ARG
  * (null state, bad counts), PIC_ERR_STATE (an emitter is set: the slot count would grow),
  * PIC_ERR_CUDA.  The host buffer must stay untouched until the stream reaches that point. */
 pic_status pic_step_host(pic_sim *s, void *host_state, int64_t n_slots, int64_t n_steps,
