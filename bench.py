@@ -1014,7 +1014,7 @@ def main():
             line["fp64"] = measure_fp64(pic, wl, dt, peak)
             line["m2"] = measure_m2()
             if args.batched:
-                line["batched"] = sweep_measure(args.batched, 64, 16)
+                line["batched"] = sweep_measure(args.batched, 320, 32)
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()
