@@ -960,7 +960,8 @@ def main():
     # pinned memory, steps and reads it back (pic_step_host)
     n_slots = pic.pic_particles_count(sim)
     bpp = pic.pic_particles_raw_bytes(sim)
-    host = torch.empty(n_slots * bpp, dtype=torch.uint8, pin_memory=True)
+    host = torch.empty(pic.pic_particles_raw_size(sim, n_slots), dtype=torch.uint8,
+                       pin_memory=True)
     pic.pic_particles_raw_get(sim, host.data_ptr(), n_slots)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)

@@ -402,12 +402,19 @@ pic_status pic_particles_get(pic_sim *s, int64_t n_cap, int64_t *pid, int32_t *t
 /* Raw device state, for host round trips in the storage format: FP32 slots take 24 bytes
  * (int32 tri, int32 lambda_0, int32 lambda_1 at 2^-22, float u_rho, u_phi, u_z), FP64
  * slots 44 bytes (int32 tri, double lambda_0, lambda_1, u_rho, u_phi, u_z), stored as
- * structure-of-arrays over n_slots: all tri values, then all lambda_0, and so on.
+ * structure-of-arrays with a stride of n_slots rounded up to a multiple of 32 slots: all
+ * tri values, then (from byte 4 * stride) all lambda_0, and so on, so that every array
+ * starts on a 128-byte boundary of the buffer (host -> device copies from less aligned
+ * starts run ~15% slower).  A buffer for n_slots slots holds pic_particles_raw_size bytes
+ * (stride x bytes per slot); the padding slots are neither read nor written.
  * pic_particles_raw_get copies the first n_slots slots device -> host (n_slots at most
  * the count from pic_particles_count); pic_particles_raw_set copies n_slots slots host ->
  * device and makes n_slots the slot count (at most the capacity; particle ids are kept).
  * Both are asynchronous on the stream; host buffers should be page-locked. */
 pic_status pic_particles_raw_bytes(pic_sim *s, int64_t *bytes_per_particle);
+/* Bytes of a raw host buffer of n_slots slots (the layout above).  Errors: ARG (null
+ * output, negative count). */
+pic_status pic_particles_raw_size(pic_sim *s, int64_t n_slots, int64_t *bytes);
 pic_status pic_particles_raw_get(pic_sim *s, void *host_dst, int64_t n_slots,
                                  void *cuda_stream);
 pic_status pic_particles_raw_set(pic_sim *s, const void *host_src, int64_t n_slots,

@@ -74,6 +74,10 @@ struct SimBase {
     virtual pic_status get(int64_t cap, int64_t *pid, int32_t *tri, double *lam, double *u,
                            cudaStream_t s) = 0;
     virtual int64_t raw_bytes() const = 0;
+    // slots per array in the raw host layout: n rounded up to 32, so that every array
+    // starts on a 128-byte boundary (host -> device copies from a less aligned start ran
+    // at 177 instead of 210 GB/s)
+    static int64_t raw_stride(int64_t n) { return (n + 31) / 32 * 32; }
     virtual pic_status raw_get(void *dst, int64_t n, cudaStream_t s) = 0;
     virtual pic_status raw_set(const void *src, int64_t n, cudaStream_t s) = 0;
     virtual pic_status step_host(void *state, int64_t n, int64_t steps, cudaStream_t s) = 0;
@@ -1324,20 +1328,7 @@ struct SimImpl final : SimBase {
             set_error("pic_particles_raw_get: bad argument");
             return PIC_ERR_ARG;
         }
-        char *h = static_cast<char *>(dst);
-        const Particles<P> &p = parts[cur];
-        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.tri, 4 * n, cudaMemcpyDeviceToHost, s));
-        h += 4 * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.l0, sizeof(Lam) * n, cudaMemcpyDeviceToHost, s));
-        h += sizeof(Lam) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.l1, sizeof(Lam) * n, cudaMemcpyDeviceToHost, s));
-        h += sizeof(Lam) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.ur, sizeof(R) * n, cudaMemcpyDeviceToHost, s));
-        h += sizeof(R) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.up, sizeof(R) * n, cudaMemcpyDeviceToHost, s));
-        h += sizeof(R) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(h, p.uz, sizeof(R) * n, cudaMemcpyDeviceToHost, s));
-        return PIC_OK;
+        return copy_slots(static_cast<char *>(dst), n, 0, n, false, s);
     }
 
     pic_status raw_set(const void *src, int64_t n, cudaStream_t s) override {
@@ -1345,26 +1336,18 @@ struct SimImpl final : SimBase {
             set_error("pic_particles_raw_set: bad argument");
             return PIC_ERR_ARG;
         }
-        const char *h = static_cast<const char *>(src);
-        const Particles<P> &p = parts[cur];
-        PIC_CUDA_TRY(cudaMemcpyAsync(p.tri, h, 4 * n, cudaMemcpyHostToDevice, s));
-        h += 4 * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(p.l0, h, sizeof(Lam) * n, cudaMemcpyHostToDevice, s));
-        h += sizeof(Lam) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(p.l1, h, sizeof(Lam) * n, cudaMemcpyHostToDevice, s));
-        h += sizeof(Lam) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(p.ur, h, sizeof(R) * n, cudaMemcpyHostToDevice, s));
-        h += sizeof(R) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(p.up, h, sizeof(R) * n, cudaMemcpyHostToDevice, s));
-        h += sizeof(R) * n;
-        PIC_CUDA_TRY(cudaMemcpyAsync(p.uz, h, sizeof(R) * n, cudaMemcpyHostToDevice, s));
+        // copy_slots only reads the host buffer on the way up
+        pic_status st = copy_slots(const_cast<char *>(static_cast<const char *>(src)), n, 0, n,
+                                   true, s);
+        if (st != PIC_OK) return st;
         PIC_CUDA_TRY(cudaMemcpyAsync(d_n, &n, sizeof(int64_t), cudaMemcpyHostToDevice, s));
         n_bound = emitting ? cap : n;
         dgl_dirty = true;
         return PIC_OK;
     }
 
-    // slots [c0, c1) of the raw state, host <-> device (one copy per array)
+    // slots [c0, c1) of the raw state, host <-> device (one copy per array; array k starts
+    // at sum_{j<k} size_j * raw_stride(n) bytes of the host buffer)
     pic_status copy_slots(char *h, int64_t n, int64_t c0, int64_t c1, bool up, cudaStream_t s) {
         const Particles<P> &p = parts[cur];
         void *dev[6] = {p.tri, p.l0, p.l1, p.ur, p.up, p.uz};
@@ -1375,7 +1358,7 @@ struct SimImpl final : SimBase {
             const size_t bytes = sz[k] * (size_t)(c1 - c0);
             if (up) PIC_CUDA_TRY(cudaMemcpyAsync(d, hk, bytes, cudaMemcpyHostToDevice, s));
             else PIC_CUDA_TRY(cudaMemcpyAsync(hk, d, bytes, cudaMemcpyDeviceToHost, s));
-            h += sz[k] * n;
+            h += sz[k] * raw_stride(n);
         }
         return PIC_OK;
     }
@@ -1755,6 +1738,17 @@ extern "C" pic_status pic_particles_raw_bytes(pic_sim *s, int64_t *b) try {
     return PIC_OK;
 }
 PIC_CATCH("pic_particles_raw_bytes")
+
+extern "C" pic_status pic_particles_raw_size(pic_sim *s, int64_t n_slots, int64_t *bytes) try {
+    SIM_CHECK(s, "pic_particles_raw_size");
+    if (!bytes || n_slots < 0) {
+        set_error("pic_particles_raw_size: bad argument");
+        return PIC_ERR_ARG;
+    }
+    *bytes = SimBase::raw_stride(n_slots) * s->impl->raw_bytes();
+    return PIC_OK;
+}
+PIC_CATCH("pic_particles_raw_size")
 
 extern "C" pic_status pic_particles_raw_get(pic_sim *s, void *dst, int64_t n, void *st) try {
     SIM_CHECK(s, "pic_particles_raw_get");

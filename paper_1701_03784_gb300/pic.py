@@ -103,6 +103,7 @@ _SIGS = {
     "pic_particles_count": [_P, _P, _P],
     "pic_particles_get": [_P, _I64, _P, _P, _P, _P, _P],
     "pic_particles_raw_bytes": [_P, _P],
+    "pic_particles_raw_size": [_P, _I64, _P],
     "pic_particles_raw_get": [_P, _P, _I64, _P],
     "pic_particles_raw_set": [_P, _P, _I64, _P],
     "pic_step_host": [_P, _P, _I64, _I64, _P],
@@ -537,8 +538,17 @@ def pic_particles_raw_bytes(sim):
     return b.value
 
 
+def pic_particles_raw_size(sim, n_slots):
+    """Bytes of a raw host buffer of n_slots slots (each array starts on a 128-byte
+    boundary: the per-array stride is n_slots rounded up to 32)."""
+    b = ctypes.c_int64()
+    _check(_lib.pic_particles_raw_size(sim.ptr, int(n_slots), ctypes.byref(b)),
+           "pic_particles_raw_size")
+    return b.value
+
+
 def pic_particles_raw_get(sim, host_ptr, n_slots, stream=None):
-    """host_ptr: address (int) of a page-locked buffer of n_slots * raw_bytes bytes."""
+    """host_ptr: address (int) of a page-locked buffer of pic_particles_raw_size bytes."""
     _check(_lib.pic_particles_raw_get(sim.ptr, ctypes.c_void_p(host_ptr), int(n_slots),
                                       _stream(stream)), "pic_particles_raw_get")
 
@@ -550,7 +560,7 @@ def pic_particles_raw_set(sim, host_ptr, n_slots, stream=None):
 
 def pic_step_host(sim, host_ptr, n_slots, n_steps=1, stream=None):
     """n_steps steps with the raw state in the page-locked host buffer at host_ptr
-    (n_slots * raw_bytes bytes): uploaded, stepped and written back every step."""
+    (pic_particles_raw_size bytes): uploaded, stepped and written back every step."""
     _check(_lib.pic_step_host(sim.ptr, ctypes.c_void_p(host_ptr), int(n_slots), int(n_steps),
                               _stream(stream)), "pic_step_host")
 

@@ -268,7 +268,10 @@ def test_raw_roundtrip(pic, cavity_oracle):
     n = pic.pic_particles_count(sim)
     b = pic.pic_particles_raw_bytes(sim)
     assert b == 24
-    buf = torch.empty(n * b, dtype=torch.uint8, pin_memory=True)
+    # every array of the raw layout starts on a 128-byte boundary
+    for m in (0, 1, 31, 32, 33, n):
+        assert pic.pic_particles_raw_size(sim, m) == -(-m // 32) * 32 * b
+    buf = torch.empty(pic.pic_particles_raw_size(sim, n), dtype=torch.uint8, pin_memory=True)
     before = pic.pic_particles_get(sim)
     pic.pic_particles_raw_get(sim, buf.data_ptr(), n)
     torch.cuda.synchronize()
@@ -323,7 +326,8 @@ def test_step_host_matches_device_steps(pic, cavity_oracle, prec):
                                    sort_interval=3)
         nslot = pic.pic_particles_count(sim)
         bpp = pic.pic_particles_raw_bytes(sim)
-        host = torch.empty(nslot * bpp, dtype=torch.uint8, pin_memory=True)
+        host = torch.empty(pic.pic_particles_raw_size(sim, nslot), dtype=torch.uint8,
+                           pin_memory=True)
         pic.pic_particles_raw_get(sim, host.data_ptr(), nslot)
         torch.cuda.synchronize()
         if mode == "device":
@@ -336,17 +340,19 @@ def test_step_host_matches_device_steps(pic, cavity_oracle, prec):
         order = np.argsort(g["pid"])
         if mode == "host":
             live = pic.pic_particles_count(sim)
-            back = torch.empty(nslot * bpp, dtype=torch.uint8, pin_memory=True)
+            back = torch.empty(pic.pic_particles_raw_size(sim, nslot), dtype=torch.uint8,
+                               pin_memory=True)
             pic.pic_particles_raw_get(sim, back.data_ptr(), live)
             torch.cuda.synchronize()
             # per array: the first `live` slots of the returned buffer are the device state
+            # (array strides: the slot counts rounded up to 32)
             sizes = [4] + [(bpp - 4) // 5] * 5       # tri, then 5 arrays of one type
             hb, bb = host.numpy(), back.numpy()
             off_h = off_b = 0
             for sz in sizes:
                 assert np.array_equal(hb[off_h:off_h + sz * live], bb[off_b:off_b + sz * live])
-                off_h += sz * nslot
-                off_b += sz * live
+                off_h += sz * (-(-nslot // 32) * 32)
+                off_b += sz * (-(-live // 32) * 32)
         runs.append(({k: g[k][order] for k in ("pid", "tri", "lam", "u")}, d))
     (g1, d1), (g2, d2) = runs
     assert d1["n_absorbed"] > 0 and d1["n_absorbed"] == d2["n_absorbed"]
