@@ -38,6 +38,7 @@ namespace {
 constexpr int TM = 128;       // samples per tile = MMA M
 constexpr int NTILE = 2;      // tiles per CTA (ping-pong)
 constexpr int EPI_WARPS = 8;  // per tile: two per TMEM lane quadrant, each half the columns
+constexpr int PARTS = EPI_WARPS / 4;   // column parts per lane quadrant
 constexpr int CTRL_WARP = NTILE * EPI_WARPS;   // lane 0 issues the products
 constexpr int LOAD_WARP = CTRL_WARP + 1;       // lane 0 streams the weights
 constexpr int NTH = (LOAD_WARP + 1) * 32;
@@ -383,14 +384,14 @@ __global__ void __launch_bounds__(NTH, MIN_BLOCKS) k_mlp_tc(MlpTc tc, const floa
     } else {
         // ---- epilogues: warps 8t .. 8t+7 own tile t ----------------------------------------
         const int t = warp / EPI_WARPS, w = warp % EPI_WARPS;
-        const int quad = w & 3, half = w >> 2;
+        const int quad = w & 3, part = w >> 2;
         const int erow = quad * 32 + lane;
         const long long row = pair0 + (long long)t * TM + erow;
         uint16_t *act = sm.a[t];
         // layer-0 operand: the two warps of a quadrant split its 32 rows' columns
         {
             const int k0 = tc.k[0], kp = tc.kp[0];
-            for (int cc = half * 8; cc < kp; cc += 16) {
+            for (int cc = part * 8; cc < kp; cc += 8 * PARTS) {
                 float v[8];
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
@@ -413,8 +414,11 @@ __global__ void __launch_bounds__(NTH, MIN_BLOCKS) k_mlp_tc(MlpTc tc, const floa
             }
             fence_after();
             const float *bias = sm.bias + tc.boff[l];
-            const int chunks = np / 16, c0 = half ? (chunks + 1) / 2 : 0;
-            const int c1 = half ? chunks : (chunks + 1) / 2;
+            // this warp's 16-column chunks: part p of PARTS (rounded so that two parts
+            // split an odd count with the larger share first)
+            const int chunks = np / 16;
+            const int c0 = (chunks * part + PARTS - 1) / PARTS;
+            const int c1 = (chunks * (part + 1) + PARTS - 1) / PARTS;
             const unsigned lane_base = tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(t * 256);
             if (!last && c0 < c1) {
                 // hidden layer: the next chunk's TMEM load is in flight while this one is
